@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Throughput of the noise -> Zel'dovich path (grid cells per second) on GB300.
+
+One step = one pass of the whole path over one grid: Philox white noise,
+forward r2c 3-D transform, Eq. 1 filter, then for each component j the Eq. 2
+filter, the c2r transform and the Eq. 3 epilogue writing positions and
+velocities (Ginnungagap, arXiv:2511.10353, Secs. 2.1-2.2).
+
+Default workload: 512^3 cells, L = 500 Mpc/h, BBKS (Om=.3, h=.7, ns=.96,
+s8=.8), z = 100, FP32, outputs pos + vel (3 + 3 grids). The working set
+(>= 4.3 GB) is far larger than the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+Prints one JSON line (rank 0). Under torchrun each rank runs an independent
+replica (the path has no exchange step on one GPU): value = cells of all
+ranks / max-over-ranks time, scaling "weak".
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid cells/sec noise->Zel'dovich (FP32 vs FP64 plain), % HBM roofline, err vs FP64"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram bytes (read + write) per launch of the dominant kernel from one ncu
+# capture, scaled to the bench workload, with the hash of the kernel sources it
+# was taken on; reported as null when the sources have changed since.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gg_device.cuh", "gg_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2511_10353_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="zeldovich_512_fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def config_of(w, outputs="pos+vel"):
+    return {"workload": "zeldovich_%d_%s" % (w["n"], w["prec"].replace("f", "fp")),
+            "n": w["n"], "box_mpc_h": w["box"], "transfer": w["cosmo"]["tf"],
+            "omega_m": w["cosmo"]["omega_m"], "z_init": w["z_init"], "outputs": outputs,
+            "cells_per_step": w["n"] ** 3,
+            "l2": "working set > L2 (129 MB), no flush", "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(w, n_s):
+    """The oracle on an n_s^3 grid with the workload's cell size: (seconds, cells)."""
+    from oracle import fields
+    from oracle.cosmology import Cosmology
+    c = w["cosmo"]
+    cosmo = Cosmology(c["omega_m"], c["h"], c["n_s"], c["sigma_8"], tf=c["tf"],
+                      omega_b=c.get("omega_b", 0.049), t_cmb=c.get("t_cmb", 2.7255))
+    cosmo.amplitude()
+    box = w["box"] * n_s / w["n"]
+    t0 = time.perf_counter()
+    fields.zeldovich(n_s, box, cosmo, w["z_init"], seed=w["seed"])
+    return time.perf_counter() - t0, n_s ** 3
+
+
+def cpu_baseline(w, n_s=256):
+    from oracle.fields import WORKERS
+    secs, cells = oracle_sample(w, n_s)
+    return {"value": cells / secs, "unit": "cells/s", "cores": WORKERS, "kind": "oracle",
+            "sample": "one %d^3 realization (box %.1f Mpc/h, same cell size and cosmology), "
+                      "FP64 numpy/scipy; noise single-threaded, FFTs on %d scipy workers; %.1f s"
+                      % (n_s, w["box"] * n_s / w["n"], WORKERS, secs)}
+
+
+def run_reference(args, w):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    n_s = 128 if per_step_budget >= 1.5 else (64 if per_step_budget >= 0.15 else 32)
+    for _ in range(args.warmup):
+        oracle_sample(w, n_s)
+    total, cells = 0.0, 0
+    for _ in range(args.steps):
+        s, c = oracle_sample(w, n_s)
+        total += s
+        cells += c
+    value = cells / total
+    from oracle.fields import WORKERS
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w),
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": WORKERS, "kind": "oracle",
+                             "sample": "each step one %d^3 realization with the workload's cell "
+                                       "size and cosmology (FP64 numpy/scipy oracle)" % n_s},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    from paper_2511_10353_gb300.workloads import WORKLOADS
+    w = dict(WORKLOADS[args.workload])
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import paper_2511_10353_gb300 as gg
+    from paper_2511_10353_gb300 import build
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build(verbose=False)
+    if dist:
+        dist.barrier()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    n = w["n"]
+    cells = n ** 3
+    plan = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], w["prec"])
+    dt = plan.dtype
+    shape = (n, n, n)
+    out = {"psi": [None] * 3,
+           "pos": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)],
+           "vel": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)]}
+    stream = torch.cuda.current_stream()
+    for i in range(max(3, args.warmup)):
+        plan.zeldovich(seed=1 + i, out=out)
+    plan.sync()
+    # timed region: K steps, per-kernel events on the plan's (= current) stream
+    plan.set_profiling(True)
+    plan.profile(reset=True)
+    dev_props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    gpu_id = "GPU-" + str(dev_props.uuid) if getattr(dev_props, "uuid", None) else str(local_rank)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        plan.zeldovich(seed=1 + i, out=out)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    plan.sync()
+    prof = plan.profile(reset=True)
+    plan.set_profiling(False)
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * cells * args.steps / (ms * 1e-3)
+    launches = sum(v["launches"] for v in prof.values())
+
+    peak, peak_src = peak_hbm()
+    kernels = {}
+    for name, v in prof.items():
+        per = v["ms"] / v["launches"]
+        gbs = v["bytes"] / (per * 1e-3) / 1e9
+        kernels[name] = {"ms_per_launch": per, "launches": v["launches"], "GB_s": gbs,
+                         "share": v["ms"] / sum(x["ms"] for x in prof.values())}
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dper = prof[dom]["ms"] / prof[dom]["launches"]
+    achieved = prof[dom]["bytes"] / (dper * 1e-3) / 1e9
+    traffic = None
+    rec = NCU_TRAFFIC.get((dom, args.workload))
+    if rec and rec[1] == kernel_source_hash():
+        traffic = rec[0]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": prof[dom]["bytes"], "traffic": traffic}
+    step_bytes = sum(v["bytes"] * v["launches"] for v in prof.values()) / args.steps
+    path_gbs = step_bytes / (ms / args.steps * 1e-3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if w["prec"] == "f32" else "f64", "data": "synthetic",
+            "config": config_of(w), "roofline": roofline,
+            "path": {"algorithmic_bytes_per_cell": step_bytes / cells, "GB_s": path_gbs,
+                     "frac_of_peak": path_gbs / peak},
+            "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
+
+    # FP64 plain path on the same workload, and the FP32 error against it
+    if not args.no_fp64 and w["prec"] == "f32":
+        plan64 = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], "f64")
+        k64 = max(2, min(10, args.steps // 10))
+        psi64 = torch.empty(shape, dtype=torch.float64, device="cuda")
+        psi32 = torch.empty(shape, dtype=torch.float32, device="cuda")
+        errs = []
+        for j in range(3):
+            o64 = {"psi": [psi64 if c == j else None for c in range(3)], "pos": [None] * 3,
+                   "vel": [None] * 3}
+            o32 = {"psi": [psi32 if c == j else None for c in range(3)], "pos": [None] * 3,
+                   "vel": [None] * 3}
+            plan64.zeldovich(seed=1, out=o64)
+            plan.zeldovich(seed=1, out=o32)
+            torch.cuda.synchronize()
+            errs.append(float(torch.linalg.vector_norm(psi32.double() - psi64)
+                              / torch.linalg.vector_norm(psi64)))
+        del psi64, psi32
+        out64 = {"psi": [None] * 3,
+                 "pos": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)],
+                 "vel": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)]}
+        plan64.zeldovich(seed=1, out=out64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k64):
+            plan64.zeldovich(seed=1 + i, out=out64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        v64 = cells / (ms64 * 1e-3)
+        line["fp64"] = {"value": v64, "unit": "cells/s", "ms_per_step": ms64, "steps": k64,
+                        "fp32_speedup": (value / world) / v64}
+        line["err_vs_fp64"] = {"psi_rel_l2": errs, "reference": "GPU FP64 path (within 1e-12 "
+                               "of the FP64 oracle in tests/test_gpu_fullsize.py)"}
+        del out64, plan64
+        torch.cuda.empty_cache()
+
+    # end to end through the public API with host buffers: caller white noise
+    # (the paper's "WN from file" input) up, positions and velocities down
+    if not args.no_e2e:
+        hn = torch.randn(shape, dtype=dt).pin_memory()
+        hout = {"psi": [None] * 3,
+                "pos": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)],
+                "vel": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)]}
+        del out
+        torch.cuda.empty_cache()
+        ke = max(2, min(8, args.steps // 10))
+        plan.zeldovich_host(noise=hn, out=hout)
+        barrier()
+        t = time.perf_counter()
+        for i in range(ke):
+            plan.zeldovich_host(noise=hn, out=hout)
+        el = time.perf_counter() - t
+        if dist:
+            tt = torch.tensor([el], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        esz = torch.finfo(dt).bits // 8
+        line["e2e"] = {"value": world * cells * ke / el, "unit": "cells/s", "steps": ke,
+                       "h2d_bytes_per_step": cells * esz, "d2h_bytes_per_step": 6 * cells * esz,
+                       "api": "gg_zeldovich_host (pinned host noise in, pos/vel out)"}
+
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

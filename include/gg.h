@@ -1,0 +1,210 @@
+/*
+ * gg.h -- C ABI of the GB300 (sm_103a) Zel'dovich initial-conditions path.
+ *
+ * The method is that of Ginnungagap (arXiv:2511.10353): Gaussian white noise
+ * on a periodic N^3 grid (Sec. 2, step 1) is convolved with the square root
+ * of the power spectrum in Fourier space (Sec. 2.1, Eq. 1), turned into the
+ * three displacement/velocity-field components psi~_j = i k_j delta~ / k^2
+ * (Eq. 2) and finally into Zel'dovich particle positions and velocities
+ * (Sec. 2.2, Eq. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid:  N points per axis (N even, N = 2^a 3^b, 4 <= N <= 4096), box side
+ *        L [Mpc/h], cell Delta = L/N. Real fields are N^3 arrays in C order
+ *        with z fastest: idx = (i_x N + i_y) N + i_z.
+ * Type:  GG_F32 -> float, GG_F64 -> double for every real array of a plan.
+ * Noise: W(idx) from Philox4x32-10 (Salmon et al., SC'11) with counter
+ *        (g_lo, g_hi, 0, 0), g = idx >> 2, key (seed_lo, seed_hi); lane
+ *        idx & 3 selects one output of the two Box-Muller pairs
+ *        (u_a = (r_2p + 1) 2^-32, u_b = r_2p+1 2^-32, p = lane >> 1;
+ *        W = sqrt(-2 ln u_a) cos(2 pi u_b) for even lanes, sin for odd).
+ * Fourier: forward transform orthonormal, inverse unnormalised; the filter
+ *        is D(z) sqrt(P(k)/V), V = L^3. Modes with k = 0 or any |m_j| = N/2
+ *        are zeroed.
+ * Output: psi_j = displacement [Mpc/h] (carries D(z)); pos_j = (q_j + psi_j)
+ *        mod L with q_j = (i_j + 1/2) Delta (or i_j Delta with GG_Q_CORNER);
+ *        vel_j = 100 a E(a) f(a) psi_j [km/s, peculiar].
+ *
+ * Memory ownership: the caller owns every input/output buffer; device
+ * pointers must be CUDA device memory on the plan's device, aligned to 16
+ * bytes. The plan owns its workspace and FP64-generated tables.
+ *
+ * Asynchrony: compute calls enqueue work on the plan's stream and return at
+ * once. Argument errors return GG_EINVAL before anything is enqueued. Launch
+ * errors return GG_ECUDA. Errors detected on the device (an exceeded wait
+ * budget, a bounds violation in a checking build) are latched in a device
+ * word and returned by the next gg_sync().
+ *
+ * Thread safety: a plan may be used by one host thread at a time. Distinct
+ * plans are independent.
+ */
+#ifndef GG_H
+#define GG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GG_OK = 0,
+  GG_EINVAL = -1,   /* invalid argument; nothing enqueued */
+  GG_ENOMEM = -2,   /* device or host allocation failed */
+  GG_ECUDA = -3,    /* a CUDA runtime call or a kernel launch failed */
+  GG_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+  GG_EDEVICE = -5   /* the device reported an error (bounds check) */
+} gg_status;
+
+typedef enum { GG_F32 = 0, GG_F64 = 1 } gg_prec;
+
+typedef enum {
+  GG_TF_BBKS = 0,        /* Bardeen, Bond, Kaiser & Szalay (1986) eq. G3, q = k/(Om h) */
+  GG_TF_EH_NOWIGGLE = 1, /* Eisenstein & Hu (1998) eqs. 26, 28-31 */
+  GG_TF_TABLE = 2        /* caller's tabulated P(k, z=0), log-log interpolated */
+} gg_tf;
+
+/* Lagrangian lattice at cell corners (q = i Delta) instead of centres. */
+#define GG_Q_CORNER 0x1u
+
+/* Cosmological parameters and power spectrum (Sec. 2.1: "cosmological
+ * parameters and the power spectrum in tabulated form"). */
+typedef struct {
+  double omega_m;  /* matter density today, > 0 */
+  double omega_l;  /* Lambda today; < 0 means 1 - omega_m (flat) */
+  double omega_b;  /* baryons (EH no-wiggle only) */
+  double h;        /* H0 / (100 km/s/Mpc), > 0 */
+  double n_s;      /* primordial spectral index */
+  double sigma_8;  /* > 0: normalise sigma(8 Mpc/h, z=0); 0 with GG_TF_TABLE: keep the
+                      table's amplitude */
+  double t_cmb;    /* CMB temperature [K] (EH no-wiggle only) */
+  int32_t tf;      /* gg_tf */
+  int32_t reserved;
+  const double *tab_k; /* GG_TF_TABLE: k [h/Mpc], strictly increasing, host memory */
+  const double *tab_p; /* GG_TF_TABLE: P(k, z=0) [(Mpc/h)^3] > 0, host memory */
+  int64_t tab_n;       /* GG_TF_TABLE: number of table rows, >= 2 */
+} gg_cosmo;
+
+/* One problem: grid, box, precision, cosmology, initial redshift. */
+typedef struct {
+  int64_t n;        /* grid points per axis */
+  double box;       /* L [Mpc/h] > 0 */
+  int32_t prec;     /* gg_prec */
+  uint32_t flags;   /* GG_Q_CORNER */
+  gg_cosmo cosmo;
+  double z_init;    /* initial redshift >= 0 */
+  double growth_override[2]; /* {D(z)/D(0), f(z)}; NaN entries are computed (FP64) */
+} gg_params;
+
+/* Scalars a plan derived from its parameters on the host in FP64. */
+typedef struct {
+  double a;          /* 1/(1+z_init) */
+  double growth;     /* D(a)/D(1) */
+  double growth_rate;/* f = dlnD/dlna */
+  double hubble;     /* E(a) = H(a)/H0 */
+  double vfac;       /* 100 a E f: km/s per Mpc/h of displacement */
+  double amplitude;  /* A in P(k, 0) = A k^n_s T(k)^2 (or the table scale) */
+  double sigma_8;    /* sigma(8 Mpc/h) of the normalised P at z = 0 */
+  int64_t n;
+  int64_t workspace_bytes;
+} gg_info;
+
+typedef struct gg_plan gg_plan_t;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int gg_version(void);
+
+/* Validate *p and compute the derived FP64 scalars on the host (no device use).
+ * Returns GG_EINVAL for invalid parameters. */
+gg_status gg_cosmo_eval(const gg_params *p, gg_info *out);
+
+/* Normalised linear P(k) at z = 0 [(Mpc/h)^3] at `count` wavenumbers k [h/Mpc]
+ * (host arrays). Host only: the same FP64 code that fills a plan's tables. */
+gg_status gg_power(const gg_params *p, const double *k, double *pk, int64_t count);
+
+/* The FP64 density filter S(m2) = D sqrt(P(2 pi sqrt(m2)/L) / V) for integer
+ * m2 = 0 .. count-1 (S(0) = 0), before the N^-3/2 transform factor. Host only. */
+gg_status gg_filter_table(const gg_params *p, double *s, int64_t count);
+
+/* Device bytes a plan for *p allocates (workspace + tables). Host only. */
+gg_status gg_workspace_size(const gg_params *p, size_t *bytes);
+
+/* Create a plan on the current CUDA device: validates *p, computes the FP64
+ * scalars and tables (Sec. 2.1 inputs), allocates the workspace.
+ * `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * On failure *plan is NULL and the status says why. */
+gg_status gg_plan(gg_plan_t **plan, const gg_params *p, void *stream);
+
+/* Change the stream later calls enqueue on. */
+gg_status gg_set_stream(gg_plan_t *plan, void *stream);
+
+/* Derived scalars of a plan. */
+gg_status gg_plan_info(const gg_plan_t *plan, gg_info *out);
+
+/* Sec. 2, step 1: write W(idx) for all N^3 cells to noise_dev (N^3 reals of the
+ * plan's type, caller-owned device memory). */
+gg_status gg_white_noise(gg_plan_t *plan, uint64_t seed, void *noise_dev);
+
+/* Raw Philox4x32-10 words for group counters first_group .. first_group+count-1
+ * under `seed`: out_dev[4 i + w] = word w of counter first_group + i
+ * (uint32, device memory, 4*count entries). `stream` as in gg_plan. The
+ * integers behind W are bit-exact and independent of launch shape. */
+gg_status gg_noise_bits(uint64_t seed, int64_t first_group, int64_t count, uint32_t *out_dev,
+                        void *stream);
+
+/* Sec. 2.1, Eq. 1: the density field delta(x) = sum_k delta~(k) e^{ik.x} with
+ * delta~ = D sqrt(P/V) W~. noise_dev = NULL generates W from `seed` inside the
+ * first transform pass; otherwise noise_dev (N^3 reals) is read and `seed`
+ * ignored. delta_dev: N^3 reals, caller-owned. */
+gg_status gg_gaussian_field(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
+                            void *delta_dev);
+
+/* Secs. 2.1-2.2, Eqs. 1-3: noise -> delta~ -> psi_j (one component at a time)
+ * -> Zel'dovich positions and velocities. Each of psi_dev[j], pos_dev[j],
+ * vel_dev[j] (j = x, y, z) is NULL or an N^3-real device buffer; a component
+ * with all three NULL is skipped. noise_dev as in gg_gaussian_field. The
+ * arrays psi_dev, pos_dev, vel_dev themselves may be NULL (= all NULL). */
+gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
+                       void *const psi_dev[3], void *const pos_dev[3], void *const vel_dev[3]);
+
+/* gg_zeldovich with HOST buffers (pinned memory recommended): copies
+ * noise_host (NULL = generate from seed) to the device, runs the path and
+ * copies each requested output back, overlapping the copy of component j with
+ * the compute of component j+1. Synchronous: returns when the outputs are in
+ * host memory. */
+gg_status gg_zeldovich_host(gg_plan_t *plan, uint64_t seed, const void *noise_host,
+                            void *const psi_host[3], void *const pos_host[3],
+                            void *const vel_host[3]);
+
+/* Per-kernel timing: with `enable` != 0 every launch of the plan is bracketed
+ * by CUDA events recorded on the plan's stream (the stream the kernel runs
+ * on); gg_profile_read reports the accumulated device time per kernel kind. */
+gg_status gg_set_profiling(gg_plan_t *plan, int enable);
+
+/* Accumulated device time of each kernel kind since the last reset. On entry
+ * *count is the capacity of the arrays; on return the number of kinds
+ * written. names[i] are static strings; ms[i] the summed milliseconds;
+ * launches[i] the launch count; bytes[i] the algorithmic HBM bytes of one
+ * launch (compulsory reads + writes of that pass). Synchronises the plan's
+ * stream. reset != 0 clears the accumulators afterwards. */
+gg_status gg_profile_read(gg_plan_t *plan, int reset, int *count, const char **names, double *ms,
+                          int64_t *launches, double *bytes);
+
+/* Wait for the plan's stream; return the first latched device error, if any. */
+gg_status gg_sync(gg_plan_t *plan);
+
+/* Message of the last failed call on this plan (plan = NULL: of the last
+ * failed call on this host thread that had no plan). Never NULL. */
+const char *gg_last_error(const gg_plan_t *plan);
+
+/* Release the plan's device memory. NULL is ignored. The caller must make sure
+ * no enqueued work of the plan is still running (gg_sync first). */
+void gg_free(gg_plan_t *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GG_H */

@@ -1,0 +1,743 @@
+// C ABI of the Zel'dovich initial-conditions path (include/gg.h): parameter
+// validation, FP64 tables, workspace ownership and the pass schedule.
+//
+// Pass schedule of gg_zeldovich ("one component at a time", Sec. 2.1: the
+// memory for the three velocity-field components is a little over two grids):
+//   z  forward  (noise generated in registers -> half spectrum)   write 4 B/cell
+//   y  forward                                                    r+w 8 B/cell
+//   x  forward  + Eq. 1 filter -> delta~ (kept)                   r+w 8 B/cell
+//   for j in x, y, z:
+//     x inverse with Eq. 2 applied on load (delta~ -> scratch)    r+w 8 B/cell
+//     y inverse                                                   r+w 8 B/cell
+//     z inverse (c2r) + Eq. 3 epilogue -> psi_j / pos_j / vel_j   r 4 + w 4 per output
+// (FP32 byte counts; FP64 doubles them.)
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gg.h"
+#include "gg_cosmo.h"
+#include "gg_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+thread_local std::string g_thread_error;
+
+struct Tables {
+  void *tw_n = nullptr;     // length N: exp(-2 pi i t / N)
+  void *tw_half = nullptr;  // length N/2
+  void *s_delta = nullptr;  // 3 (N/2)^2 + 1 entries
+  void *g_psi = nullptr;    // 3 (N/2)^2 + 1 entries
+};
+
+}  // namespace
+
+struct gg_plan {
+  gg_params p{};
+  gg_info info{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t real_bytes = 0;  // sizeof(R)
+  int64_t cells = 0;      // N^3
+  void *work = nullptr;   // N^3 reals: half spectrum, delta~ after the forward passes
+  void *work2 = nullptr;  // N^3 reals: per-component inverse transforms
+  Tables tab;
+  int *err = nullptr;     // device error word
+  gg::FftStages st_n{}, st_half{};
+  int z_lines = 1, col_b = 1;
+  std::string last_error;
+  // host-buffer entry point: device staging of two components, a copy stream
+  void *stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  void *noise_stage = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_comp[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+  // per-kernel timing
+  struct ProfRec { int kind; cudaEvent_t a, b; };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;      // event pairs (reused)
+  size_t prof_used = 0;
+  double prof_ms[16] = {0};
+  int64_t prof_launches[16] = {0};
+  double prof_bytes[16] = {0};
+};
+
+namespace {
+
+gg_status fail(gg_plan_t *plan, gg_status st, const std::string &msg) {
+  if (plan) plan->last_error = msg;
+  else g_thread_error = msg;
+  return st;
+}
+
+gg_status cuda_fail(gg_plan_t *plan, cudaError_t e, const char *what) {
+  return fail(plan, GG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool smooth_23(int64_t n) {
+  if (n <= 0) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+std::string validate(const gg_params *p) {
+  if (!p) return "params is NULL";
+  if (p->n < 4 || p->n > 4096 || (p->n & 1) || !smooth_23(p->n))
+    return "n must be even, 4 <= n <= 4096 and of the form 2^a 3^b";
+  if (!(p->box > 0) || !std::isfinite(p->box)) return "box must be > 0";
+  if (p->prec != GG_F32 && p->prec != GG_F64) return "prec must be GG_F32 or GG_F64";
+  if (p->flags & ~GG_Q_CORNER) return "unknown flag bits";
+  const gg_cosmo &c = p->cosmo;
+  if (!(c.omega_m > 0) || !std::isfinite(c.omega_m)) return "omega_m must be > 0";
+  if (!(c.h > 0) || !std::isfinite(c.h)) return "h must be > 0";
+  if (!std::isfinite(c.n_s)) return "n_s must be finite";
+  if (c.tf != GG_TF_BBKS && c.tf != GG_TF_EH_NOWIGGLE && c.tf != GG_TF_TABLE)
+    return "unknown transfer function";
+  if (!(c.sigma_8 > 0) && !(c.tf == GG_TF_TABLE && c.sigma_8 == 0.0))
+    return "sigma_8 must be > 0 (or 0 with a table to keep its amplitude)";
+  if (c.tf == GG_TF_EH_NOWIGGLE) {
+    if (!(c.omega_b > 0) || !(c.omega_b < c.omega_m)) return "omega_b must be in (0, omega_m)";
+    if (!(c.t_cmb > 0)) return "t_cmb must be > 0";
+  }
+  if (c.tf == GG_TF_TABLE) {
+    if (!c.tab_k || !c.tab_p || c.tab_n < 2) return "table needs tab_k, tab_p and tab_n >= 2";
+    for (int64_t i = 0; i < c.tab_n; ++i) {
+      if (!(c.tab_k[i] > 0) || !(c.tab_p[i] > 0)) return "table entries must be > 0";
+      if (i && !(c.tab_k[i] > c.tab_k[i - 1])) return "tab_k must be strictly increasing";
+    }
+  }
+  if (!(p->z_init >= 0) || !std::isfinite(p->z_init)) return "z_init must be >= 0";
+  const double ol = c.omega_l < 0 ? 1.0 - c.omega_m : c.omega_l;
+  const double a = 1.0 / (1.0 + p->z_init);
+  for (double x : {a, 1.0}) {
+    const double e2 = c.omega_m / (x * x * x) + (1.0 - c.omega_m - ol) / (x * x) + ol;
+    if (!(e2 > 0)) return "E(a)^2 <= 0 between z_init and today";
+  }
+  return "";
+}
+
+gg::cosmo::Model make_model(const gg_params *p) {
+  gg::cosmo::Model m;
+  const gg_cosmo &c = p->cosmo;
+  m.om = c.omega_m;
+  m.ol = c.omega_l < 0 ? 1.0 - c.omega_m : c.omega_l;
+  m.ok = 1.0 - m.om - m.ol;
+  m.ob = c.omega_b;
+  m.h = c.h;
+  m.ns = c.n_s;
+  m.sigma8 = c.sigma_8;
+  m.tcmb = c.t_cmb;
+  m.tf = c.tf;
+  if (c.tf == GG_TF_TABLE) {
+    m.tab_k.assign(c.tab_k, c.tab_k + c.tab_n);
+    m.tab_p.assign(c.tab_p, c.tab_p + c.tab_n);
+  }
+  m.normalise();
+  return m;
+}
+
+void fill_info(const gg_params *p, const gg::cosmo::Model &m, gg_info *out) {
+  const double a = 1.0 / (1.0 + p->z_init);
+  out->a = a;
+  out->growth = std::isnan(p->growth_override[0]) ? m.growth(a) : p->growth_override[0];
+  out->growth_rate = std::isnan(p->growth_override[1]) ? m.growth_rate(a) : p->growth_override[1];
+  out->hubble = m.E(a);
+  out->vfac = 100.0 * a * out->hubble * out->growth_rate;
+  out->amplitude = m.amp;
+  out->sigma_8 = m.sigma(8.0);
+  out->n = p->n;
+}
+
+size_t table_entries(int64_t n) { return (size_t)(3 * (n / 2) * (n / 2) + 1); }
+
+size_t workspace_bytes(const gg_params *p) {
+  const size_t rb = p->prec == GG_F64 ? 8 : 4;
+  const size_t grid = (size_t)p->n * p->n * p->n * rb;
+  return 2 * grid + (size_t)(p->n + p->n / 2) * 2 * rb + 2 * table_entries(p->n) * rb + 256;
+}
+
+template <typename R>
+std::vector<R> twiddles(int len) {
+  std::vector<R> t(2 * (size_t)len);
+  for (int i = 0; i < len; ++i) {
+    // exp(-2 pi i t / len) from FP64 cos/sin of the exactly reduced angle
+    const double ang = -2.0 * kPi * (double)i / (double)len;
+    t[2 * i] = (R)std::cos(ang);
+    t[2 * i + 1] = (R)std::sin(ang);
+  }
+  return t;
+}
+
+template <typename R>
+gg_status upload(gg_plan_t *plan, void **dst, const std::vector<R> &v) {
+  cudaError_t e = cudaMalloc(dst, v.size() * sizeof(R));
+  if (e != cudaSuccess) return fail(plan, GG_ENOMEM, "cudaMalloc (tables) failed");
+  e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(R), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemcpy (tables)");
+  return GG_OK;
+}
+
+// S_delta(m2) = D sqrt(P(k)/V), k = 2 pi sqrt(m2) / L, S(0) = 0 (Eq. 1).
+void filter_values(const gg_params *p, const gg::cosmo::Model &m, double growth, double *s,
+                   int64_t count) {
+  const double vol = p->box * p->box * p->box;
+  for (int64_t i = 0; i < count; ++i) {
+    if (i == 0) { s[0] = 0.0; continue; }
+    const double k = 2.0 * kPi * std::sqrt((double)i) / p->box;
+    s[i] = growth * std::sqrt(m.power(k) / vol);
+  }
+}
+
+template <typename R>
+gg_status build_tables(gg_plan_t *plan, const gg::cosmo::Model &m) {
+  const int64_t n = plan->p.n;
+  gg_status st;
+  if ((st = upload(plan, &plan->tab.tw_n, twiddles<R>((int)n))) != GG_OK) return st;
+  if ((st = upload(plan, &plan->tab.tw_half, twiddles<R>((int)(n / 2)))) != GG_OK) return st;
+  const size_t cnt = table_entries(n);
+  std::vector<double> s(cnt);
+  filter_values(&plan->p, m, plan->info.growth, s.data(), (int64_t)cnt);
+  const double norm = 1.0 / std::pow((double)n, 1.5);  // orthonormal forward transform
+  std::vector<R> sd(cnt), gp(cnt);
+  for (size_t i = 0; i < cnt; ++i) {
+    sd[i] = (R)(s[i] * norm);
+    gp[i] = i ? (R)(plan->p.box / (2.0 * kPi * (double)i)) : (R)0;  // (L / 2 pi) / m2
+  }
+  if ((st = upload(plan, &plan->tab.s_delta, sd)) != GG_OK) return st;
+  return upload(plan, &plan->tab.g_psi, gp);
+}
+
+template <typename R>
+void choose_tiles(gg_plan_t *plan) {
+  const int n = (int)plan->p.n, half = n / 2;
+  const size_t cb = 2 * sizeof(R);
+  const size_t smem_cap = 110 * 1024;
+  // z passes: about 256 threads per CTA
+  {
+    const int P = half / plan->st_half.e;
+    int cap = std::min(gg::max_block_threads<R>(0, plan->st_half.e),
+                       gg::max_block_threads<R>(2, plan->st_half.e));
+    if (cap <= 0) cap = 256;
+    int lines = std::max(1, 256 / P);
+    while (lines > 1 && (P * lines > cap || gg::zpass_smem_bytes(half, lines, cb) > smem_cap)) lines /= 2;
+    plan->z_lines = lines;
+  }
+  // strided passes: up to 16 adjacent columns, at most 512 threads
+  {
+    const int P = n / plan->st_n.e;
+    int cap = gg::max_block_threads<R>(1, plan->st_n.e);
+    if (cap <= 0) cap = 256;
+    cap = std::min(cap, 512);
+    int b = 16;
+    while (b > 1 && (half % b != 0 || P * b > cap || gg::col_smem_bytes(n, b, cb) > smem_cap)) b /= 2;
+    plan->col_b = b;
+  }
+}
+
+void release(gg_plan_t *plan) {
+  if (!plan) return;
+  void *bufs[] = {plan->work, plan->work2, plan->tab.tw_n, plan->tab.tw_half, plan->tab.s_delta,
+                  plan->tab.g_psi, plan->err, plan->noise_stage};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  for (auto &slot : plan->stage)
+    for (void *b : slot)
+      if (b) cudaFree(b);
+  for (auto &r : plan->prof) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (plan->ev_comp[i]) cudaEventDestroy(plan->ev_comp[i]);
+    if (plan->ev_copy[i]) cudaEventDestroy(plan->ev_copy[i]);
+  }
+  if (plan->copy_stream) cudaStreamDestroy(plan->copy_stream);
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ------------------------------------------------------------ kernel timing
+enum Kind { kZFwd = 0, kYFwd, kXFwd, kXInv, kYInv, kZInv, kNoise, kNumKinds };
+const char *const kKindNames[kNumKinds] = {"z_forward_noise", "y_forward", "x_forward_filter",
+                                           "x_inverse_filter", "y_inverse", "z_inverse_epilogue",
+                                           "noise"};
+
+// Records a start event before a launch and an end event after it when the
+// plan's profiling is on; `bytes` is the launch's algorithmic HBM traffic.
+struct ProfScope {
+  gg_plan_t *plan;
+  size_t slot = (size_t)-1;
+  ProfScope(gg_plan_t *p, int kind, double bytes) : plan(p) {
+    if (!plan->prof_on) return;
+    if (plan->prof_used == plan->prof.size()) {
+      gg_plan::ProfRec r{kind, nullptr, nullptr};
+      if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+      plan->prof.push_back(r);
+    }
+    slot = plan->prof_used++;
+    plan->prof[slot].kind = kind;
+    plan->prof_bytes[kind] = bytes;
+    cudaEventRecord(plan->prof[slot].a, plan->stream);
+  }
+  ~ProfScope() {
+    if (slot != (size_t)-1) cudaEventRecord(plan->prof[slot].b, plan->stream);
+  }
+};
+
+// ----------------------------------------------------------- pass launchers
+template <typename R>
+gg_status forward_passes(gg_plan_t *plan, uint64_t seed, const void *noise) {
+  const int n = (int)plan->p.n, half = n / 2;
+  gg::ZFwdArgs z{};
+  z.noise = noise;
+  z.out = plan->work;
+  z.seed = seed;
+  z.nlines = (int64_t)n * n;
+  z.n = n;
+  z.lines_per_cta = plan->z_lines;
+  z.st = plan->st_half;
+  z.tw_half = plan->tab.tw_half;
+  z.tw_full = plan->tab.tw_n;
+  const double cb = (double)plan->cells * sizeof(R);
+  cudaError_t e;
+  {
+    ProfScope ps(plan, kZFwd, noise ? 2 * cb : cb);
+    e = gg::launch_zfwd<R>(z, plan->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(plan, e, "z forward pass");
+  gg::ColArgs c{};
+  c.src = c.dst = plan->work;
+  c.cols = plan->col_b;
+  c.inner_chunks = half / plan->col_b;
+  c.n = n;
+  c.st = plan->st_n;
+  c.tw = plan->tab.tw_n;
+  // y pass: points stride N/2, outer index x with stride N * N/2
+  c.axis = 1;
+  c.stride = half;
+  c.outer_stride = (int64_t)n * half;
+  c.filter = gg::kFiltNone;
+  {
+    ProfScope ps(plan, kYFwd, 2 * cb);
+    e = gg::launch_col<R>(c, false, plan->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(plan, e, "y forward pass");
+  // x pass + Eq. 1: points stride N * N/2, outer index ky with stride N/2
+  c.axis = 0;
+  c.stride = (int64_t)n * half;
+  c.outer_stride = half;
+  c.filter = gg::kFiltDelta;
+  c.table = plan->tab.s_delta;
+  {
+    ProfScope ps(plan, kXFwd, 2 * cb);
+    e = gg::launch_col<R>(c, false, plan->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(plan, e, "x forward pass");
+  return GG_OK;
+}
+
+// delta~ in plan->work -> inverse x (optional Eq. 2 filter) into `scratch`,
+// inverse y, inverse z with the epilogue.
+template <typename R>
+gg_status inverse_passes(gg_plan_t *plan, int comp, void *scratch, void *psi, void *pos,
+                         void *vel) {
+  const int n = (int)plan->p.n, half = n / 2;
+  gg::ColArgs c{};
+  c.src = plan->work;
+  c.dst = scratch;
+  c.cols = plan->col_b;
+  c.inner_chunks = half / plan->col_b;
+  c.n = n;
+  c.st = plan->st_n;
+  c.tw = plan->tab.tw_n;
+  c.axis = 0;
+  c.stride = (int64_t)n * half;
+  c.outer_stride = half;
+  c.filter = comp >= 0 ? gg::kFiltPsi : gg::kFiltNone;
+  c.comp = comp;
+  c.table = plan->tab.g_psi;
+  const double cb = (double)plan->cells * sizeof(R);
+  cudaError_t e;
+  {
+    ProfScope ps(plan, kXInv, 2 * cb);
+    e = gg::launch_col<R>(c, true, plan->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(plan, e, "x inverse pass");
+  c.src = c.dst = scratch;
+  c.axis = 1;
+  c.stride = half;
+  c.outer_stride = (int64_t)n * half;
+  c.filter = gg::kFiltNone;
+  {
+    ProfScope ps(plan, kYInv, 2 * cb);
+    e = gg::launch_col<R>(c, true, plan->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(plan, e, "y inverse pass");
+  gg::ZInvArgs z{};
+  z.src = scratch;
+  z.psi = psi;
+  z.pos = pos;
+  z.vel = vel;
+  z.nlines = (int64_t)n * n;
+  z.n = n;
+  z.lines_per_cta = plan->z_lines;
+  z.comp = comp < 0 ? 0 : comp;
+  z.box = plan->p.box;
+  z.cell = plan->p.box / (double)n;
+  z.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
+  z.vfac = plan->info.vfac;
+  z.st = plan->st_half;
+  z.tw_half = plan->tab.tw_half;
+  z.tw_full = plan->tab.tw_n;
+  {
+    const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
+    ProfScope ps(plan, kZInv, (1 + outs) * cb);
+    e = gg::launch_zinv<R>(z, plan->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(plan, e, "z inverse pass");
+  return GG_OK;
+}
+
+template <typename R>
+gg_status run_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise, void *const psi[3],
+                        void *const pos[3], void *const vel[3]) {
+  gg_status st = forward_passes<R>(plan, seed, noise);
+  if (st != GG_OK) return st;
+  for (int j = 0; j < 3; ++j) {
+    void *ps = psi ? psi[j] : nullptr, *po = pos ? pos[j] : nullptr, *ve = vel ? vel[j] : nullptr;
+    if (!ps && !po && !ve) continue;
+    // the psi buffer doubles as the scratch of its own component (the inverse
+    // z pass reads each line into shared memory before writing it back)
+    void *scratch = ps ? ps : plan->work2;
+    st = inverse_passes<R>(plan, j, scratch, ps, po, ve);
+    if (st != GG_OK) return st;
+  }
+  return GG_OK;
+}
+
+template <typename R>
+gg_status create(gg_plan_t *plan, const gg::cosmo::Model &m) {
+  plan->real_bytes = sizeof(R);
+  const int64_t n = plan->p.n;
+  if (!gg::make_stages((int)n, &plan->st_n) || !gg::make_stages((int)(n / 2), &plan->st_half))
+    return fail(plan, GG_EINVAL, "no FFT schedule for this n");
+  gg_status st = build_tables<R>(plan, m);
+  if (st != GG_OK) return st;
+  const size_t grid = (size_t)plan->cells * sizeof(R);
+  if (cudaMalloc(&plan->work, grid) != cudaSuccess)
+    return fail(plan, GG_ENOMEM, "cudaMalloc of the transform workspace failed");
+  if (cudaMalloc(&plan->work2, grid) != cudaSuccess)
+    return fail(plan, GG_ENOMEM, "cudaMalloc of the component workspace failed");
+  if (cudaMalloc(&plan->err, 256) != cudaSuccess)
+    return fail(plan, GG_ENOMEM, "cudaMalloc of the error word failed");
+  cudaError_t e = cudaMemset(plan->err, 0, 256);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemset");
+  choose_tiles<R>(plan);
+  plan->info.workspace_bytes = (int64_t)workspace_bytes(&plan->p);
+  return GG_OK;
+}
+
+template <typename R>
+gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void *const psi[3],
+                   void *const pos[3], void *const vel[3]) {
+  const size_t grid = (size_t)plan->cells * sizeof(R);
+  cudaError_t e;
+  if (!plan->copy_stream) {
+    if ((e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(plan, e, "cudaStreamCreate");
+    for (int i = 0; i < 2; ++i) {
+      if ((e = cudaEventCreateWithFlags(&plan->ev_comp[i], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&plan->ev_copy[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(plan, e, "cudaEventCreate");
+    }
+  }
+  const void *noise_dev = nullptr;
+  if (noise_host) {
+    if (!plan->noise_stage && cudaMalloc(&plan->noise_stage, grid) != cudaSuccess)
+      return fail(plan, GG_ENOMEM, "cudaMalloc of the noise staging buffer failed");
+    if ((e = cudaMemcpyAsync(plan->noise_stage, noise_host, grid, cudaMemcpyHostToDevice,
+                             plan->stream)) != cudaSuccess)
+      return cuda_fail(plan, e, "noise upload");
+    noise_dev = plan->noise_stage;
+  }
+  gg_status st = forward_passes<R>(plan, seed, noise_dev);
+  if (st != GG_OK) return st;
+  bool used[2] = {false, false};
+  for (int j = 0; j < 3; ++j) {
+    void *hs[3] = {psi ? psi[j] : nullptr, pos ? pos[j] : nullptr, vel ? vel[j] : nullptr};
+    if (!hs[0] && !hs[1] && !hs[2]) continue;
+    const int slot = j & 1;
+    for (int o = 0; o < 3; ++o)
+      if (hs[o] && !plan->stage[slot][o] && cudaMalloc(&plan->stage[slot][o], grid) != cudaSuccess)
+        return fail(plan, GG_ENOMEM, "cudaMalloc of an output staging buffer failed");
+    if (used[slot] && (e = cudaStreamWaitEvent(plan->stream, plan->ev_copy[slot], 0)) != cudaSuccess)
+      return cuda_fail(plan, e, "cudaStreamWaitEvent");
+    void *dv[3] = {hs[0] ? plan->stage[slot][0] : nullptr, hs[1] ? plan->stage[slot][1] : nullptr,
+                   hs[2] ? plan->stage[slot][2] : nullptr};
+    void *scratch = dv[0] ? dv[0] : plan->work2;
+    st = inverse_passes<R>(plan, j, scratch, dv[0], dv[1], dv[2]);
+    if (st != GG_OK) return st;
+    if ((e = cudaEventRecord(plan->ev_comp[slot], plan->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(plan->copy_stream, plan->ev_comp[slot], 0)) != cudaSuccess)
+      return cuda_fail(plan, e, "event ordering");
+    for (int o = 0; o < 3; ++o)
+      if (hs[o] && (e = cudaMemcpyAsync(hs[o], dv[o], grid, cudaMemcpyDeviceToHost,
+                                        plan->copy_stream)) != cudaSuccess)
+        return cuda_fail(plan, e, "output download");
+    if ((e = cudaEventRecord(plan->ev_copy[slot], plan->copy_stream)) != cudaSuccess)
+      return cuda_fail(plan, e, "cudaEventRecord");
+    used[slot] = true;
+  }
+  if ((e = cudaStreamSynchronize(plan->copy_stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(plan->stream)) != cudaSuccess)
+    return cuda_fail(plan, e, "synchronize");
+  return GG_OK;
+}
+
+}  // namespace
+
+namespace gg {
+
+bool make_stages(int len, FftStages *st) {
+  std::memset(st, 0, sizeof(*st));
+  if (len < 1) return false;
+  int a = 0, b = 0, x = len;
+  while (x % 2 == 0) { x /= 2; ++a; }
+  while (x % 3 == 0) { x /= 3; ++b; }
+  if (x != 1) return false;
+  std::vector<int> rad;
+  for (int i = 0; i < a / 3; ++i) rad.push_back(8);
+  if (a % 3 == 2) rad.push_back(4);
+  if (a % 3 == 1) rad.push_back(2);
+  for (int i = 0; i < b; ++i) rad.push_back(3);
+  if ((int)rad.size() > kMaxStages) return false;
+  int pow2 = a >= 3 ? 8 : (a == 2 ? 4 : (a == 1 ? 2 : 1));
+  st->e = pow2 * (b > 0 ? 3 : 1);
+  if (len == 1) st->e = 1;
+  st->len = len;
+  st->nstages = (int)rad.size();
+  int ns = 1;
+  for (int s = 0; s < st->nstages; ++s) {
+    st->radix[s] = rad[s];
+    st->ns[s] = ns;
+    st->ns_shift[s] = (ns & (ns - 1)) == 0 ? __builtin_ctz((unsigned)ns) : -1;
+    st->tstep[s] = len / (ns * rad[s]);
+    ns *= rad[s];
+  }
+  return true;
+}
+
+}  // namespace gg
+
+// ---------------------------------------------------------------------- C ABI
+extern "C" {
+
+int gg_version(void) { return 100; }
+
+gg_status gg_cosmo_eval(const gg_params *p, gg_info *out) {
+  const std::string msg = validate(p);
+  if (!msg.empty()) return fail(nullptr, GG_EINVAL, msg);
+  if (!out) return fail(nullptr, GG_EINVAL, "out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  const gg::cosmo::Model m = make_model(p);
+  fill_info(p, m, out);
+  out->workspace_bytes = (int64_t)workspace_bytes(p);
+  return GG_OK;
+}
+
+gg_status gg_power(const gg_params *p, const double *k, double *pk, int64_t count) {
+  const std::string msg = validate(p);
+  if (!msg.empty()) return fail(nullptr, GG_EINVAL, msg);
+  if (count < 0 || (count > 0 && (!k || !pk))) return fail(nullptr, GG_EINVAL, "bad arrays");
+  const gg::cosmo::Model m = make_model(p);
+  for (int64_t i = 0; i < count; ++i) pk[i] = m.power(k[i]);
+  return GG_OK;
+}
+
+gg_status gg_filter_table(const gg_params *p, double *s, int64_t count) {
+  const std::string msg = validate(p);
+  if (!msg.empty()) return fail(nullptr, GG_EINVAL, msg);
+  if (count < 0 || (count > 0 && !s)) return fail(nullptr, GG_EINVAL, "bad array");
+  const gg::cosmo::Model m = make_model(p);
+  gg_info info{};
+  fill_info(p, m, &info);
+  filter_values(p, m, info.growth, s, count);
+  return GG_OK;
+}
+
+gg_status gg_workspace_size(const gg_params *p, size_t *bytes) {
+  const std::string msg = validate(p);
+  if (!msg.empty()) return fail(nullptr, GG_EINVAL, msg);
+  if (!bytes) return fail(nullptr, GG_EINVAL, "bytes is NULL");
+  *bytes = workspace_bytes(p);
+  return GG_OK;
+}
+
+gg_status gg_plan(gg_plan_t **plan, const gg_params *p, void *stream) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  *plan = nullptr;
+  const std::string msg = validate(p);
+  if (!msg.empty()) return fail(nullptr, GG_EINVAL, msg);
+  gg_plan_t *pl = new (std::nothrow) gg_plan_t();
+  if (!pl) return fail(nullptr, GG_ENOMEM, "host allocation failed");
+  pl->p = *p;
+  pl->p.cosmo.tab_k = pl->p.cosmo.tab_p = nullptr;  // not retained past the call
+  pl->stream = (cudaStream_t)stream;
+  pl->cells = p->n * p->n * p->n;
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(nullptr, e, "cudaGetDevice");
+  }
+  const gg::cosmo::Model m = make_model(p);
+  fill_info(p, m, &pl->info);
+  const gg_status st = p->prec == GG_F64 ? create<double>(pl, m) : create<float>(pl, m);
+  if (st != GG_OK) {
+    g_thread_error = pl->last_error;
+    release(pl);
+    delete pl;
+    return st;
+  }
+  *plan = pl;
+  return GG_OK;
+}
+
+gg_status gg_set_stream(gg_plan_t *plan, void *stream) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  plan->stream = (cudaStream_t)stream;
+  return GG_OK;
+}
+
+gg_status gg_plan_info(const gg_plan_t *plan, gg_info *out) {
+  if (!plan || !out) return fail(nullptr, GG_EINVAL, "plan or out is NULL");
+  *out = plan->info;
+  return GG_OK;
+}
+
+gg_status gg_white_noise(gg_plan_t *plan, uint64_t seed, void *noise_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!noise_dev || !aligned16(noise_dev)) return fail(plan, GG_EINVAL, "noise_dev NULL or unaligned");
+  gg::NoiseArgs a{noise_dev, seed, plan->cells};
+  cudaError_t e;
+  {
+    ProfScope ps(plan, kNoise, (double)plan->cells * plan->real_bytes);
+    e = plan->real_bytes == 8 ? gg::launch_noise<double>(a, plan->stream)
+                              : gg::launch_noise<float>(a, plan->stream);
+  }
+  return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, "noise kernel");
+}
+
+gg_status gg_noise_bits(uint64_t seed, int64_t first_group, int64_t count, uint32_t *out_dev,
+                        void *stream) {
+  if (count < 0 || first_group < 0 || (count > 0 && (!out_dev || !aligned16(out_dev))))
+    return fail(nullptr, GG_EINVAL, "bad arguments");
+  const cudaError_t e = gg::launch_noise_bits(seed, first_group, count, out_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? GG_OK : cuda_fail(nullptr, e, "noise bits kernel");
+}
+
+gg_status gg_gaussian_field(gg_plan_t *plan, uint64_t seed, const void *noise_dev, void *delta_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!delta_dev || !aligned16(delta_dev) || (noise_dev && !aligned16(noise_dev)))
+    return fail(plan, GG_EINVAL, "delta_dev NULL or a buffer unaligned");
+  gg_status st = plan->real_bytes == 8 ? forward_passes<double>(plan, seed, noise_dev)
+                                       : forward_passes<float>(plan, seed, noise_dev);
+  if (st != GG_OK) return st;
+  // comp < 0: no Eq. 2 filter; the inverse runs in place on delta~
+  return plan->real_bytes == 8
+             ? inverse_passes<double>(plan, -1, plan->work, delta_dev, nullptr, nullptr)
+             : inverse_passes<float>(plan, -1, plan->work, delta_dev, nullptr, nullptr);
+}
+
+gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
+                       void *const psi_dev[3], void *const pos_dev[3], void *const vel_dev[3]) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (noise_dev && !aligned16(noise_dev)) return fail(plan, GG_EINVAL, "noise_dev unaligned");
+  for (int j = 0; j < 3; ++j) {
+    const void *bufs[3] = {psi_dev ? psi_dev[j] : nullptr, pos_dev ? pos_dev[j] : nullptr,
+                           vel_dev ? vel_dev[j] : nullptr};
+    for (const void *b : bufs)
+      if (b && !aligned16(b)) return fail(plan, GG_EINVAL, "output buffer unaligned");
+  }
+  return plan->real_bytes == 8 ? run_zeldovich<double>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev)
+                               : run_zeldovich<float>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev);
+}
+
+gg_status gg_zeldovich_host(gg_plan_t *plan, uint64_t seed, const void *noise_host,
+                            void *const psi_host[3], void *const pos_host[3],
+                            void *const vel_host[3]) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  return plan->real_bytes == 8 ? run_host<double>(plan, seed, noise_host, psi_host, pos_host, vel_host)
+                               : run_host<float>(plan, seed, noise_host, psi_host, pos_host, vel_host);
+}
+
+gg_status gg_set_profiling(gg_plan_t *plan, int enable) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  plan->prof_on = enable != 0;
+  return GG_OK;
+}
+
+gg_status gg_profile_read(gg_plan_t *plan, int reset, int *count, const char **names, double *ms,
+                          int64_t *launches, double *bytes) {
+  if (!plan || !count || *count < 0) return fail(nullptr, GG_EINVAL, "bad arguments");
+  cudaError_t e = cudaStreamSynchronize(plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaStreamSynchronize");
+  for (size_t i = 0; i < plan->prof_used; ++i) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, plan->prof[i].a, plan->prof[i].b);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaEventElapsedTime");
+    plan->prof_ms[plan->prof[i].kind] += t;
+    plan->prof_launches[plan->prof[i].kind] += 1;
+  }
+  plan->prof_used = 0;
+  int w = 0;
+  for (int k = 0; k < kNumKinds && w < *count; ++k) {
+    if (!plan->prof_launches[k]) continue;
+    if (names) names[w] = kKindNames[k];
+    if (ms) ms[w] = plan->prof_ms[k];
+    if (launches) launches[w] = plan->prof_launches[k];
+    if (bytes) bytes[w] = plan->prof_bytes[k];
+    ++w;
+  }
+  *count = w;
+  if (reset) {
+    for (int k = 0; k < kNumKinds; ++k) {
+      plan->prof_ms[k] = 0;
+      plan->prof_launches[k] = 0;
+    }
+  }
+  return GG_OK;
+}
+
+gg_status gg_sync(gg_plan_t *plan) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaStreamSynchronize");
+  int word = 0;
+  e = cudaMemcpy(&word, plan->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "reading the device error word");
+  if (word == 0) return GG_OK;
+  cudaMemset(plan->err, 0, sizeof(int));
+  char msg[96];
+  std::snprintf(msg, sizeof msg, "device reported error code %d", word);
+  return fail(plan, word == 2 ? GG_ETIMEOUT : GG_EDEVICE, msg);
+}
+
+const char *gg_last_error(const gg_plan_t *plan) {
+  return plan ? plan->last_error.c_str() : g_thread_error.c_str();
+}
+
+void gg_free(gg_plan_t *plan) {
+  if (!plan) return;
+  release(plan);
+  delete plan;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+// Device building blocks of the sm_103a path: complex arithmetic, the
+// Philox4x32-10 generator, the Box-Muller map, radix-2/3/4/8 butterflies and
+// one Stockham stage of an in-CTA FFT held in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gg_internal.h"
+
+namespace gg {
+
+template <typename R> struct CxOf;
+template <> struct CxOf<float> { using T = float2; };
+template <> struct CxOf<double> { using T = double2; };
+template <typename R> using Cx = typename CxOf<R>::T;
+
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ T cmulc(T a, T b) {
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T> __device__ __forceinline__ T cconj(T a) { return {a.x, -a.y}; }
+// a * (-i) and a * (+i)
+template <typename T> __device__ __forceinline__ T mul_mi(T a) { return {a.y, -a.x}; }
+template <typename T> __device__ __forceinline__ T mul_pi(T a) { return {-a.y, a.x}; }
+// a * (-i) for the forward transform, a * (+i) for the inverse
+template <bool INV, typename T> __device__ __forceinline__ T mul_wi(T a) {
+  return INV ? mul_pi(a) : mul_mi(a);
+}
+
+template <typename T> __device__ __forceinline__ T ldg_c(const T *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds of the 4x32 Philox S-box/P-box with a Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// The four Philox words of the group holding cell `idx` (group = idx >> 2).
+__device__ __forceinline__ uint4 noise_words(uint64_t seed, uint64_t group) {
+  return philox4x32_10((uint32_t)group, (uint32_t)(group >> 32), 0u, 0u, (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
+// Two-output Box-Muller (Box & Muller 1958) on each word pair of a group:
+// u_a = (r_a + 1) 2^-32 in (0, 1], u_b = r_b 2^-32; rho = sqrt(-2 ln u_a);
+// outputs rho cos(2 pi u_b), rho sin(2 pi u_b).
+__device__ __forceinline__ void gauss4(uint4 w, float out[4]) {
+  const float ua0 = fmaf(__uint2float_rn(w.x), 0x1p-32f, 0x1p-32f);
+  const float ua1 = fmaf(__uint2float_rn(w.z), 0x1p-32f, 0x1p-32f);
+  const float rho0 = sqrtf(-2.0f * logf(ua0));
+  const float rho1 = sqrtf(-2.0f * logf(ua1));
+  float s0, c0, s1, c1;
+  sincospif(2.0f * (__uint2float_rn(w.y) * 0x1p-32f), &s0, &c0);
+  sincospif(2.0f * (__uint2float_rn(w.w) * 0x1p-32f), &s1, &c1);
+  out[0] = rho0 * c0;
+  out[1] = rho0 * s0;
+  out[2] = rho1 * c1;
+  out[3] = rho1 * s1;
+}
+__device__ __forceinline__ void gauss4(uint4 w, double out[4]) {
+  const double ua0 = ((double)w.x + 1.0) * 0x1p-32;
+  const double ua1 = ((double)w.z + 1.0) * 0x1p-32;
+  const double rho0 = sqrt(-2.0 * log(ua0));
+  const double rho1 = sqrt(-2.0 * log(ua1));
+  double s0, c0, s1, c1;
+  sincospi(2.0 * ((double)w.y * 0x1p-32), &s0, &c0);
+  sincospi(2.0 * ((double)w.w * 0x1p-32), &s1, &c1);
+  out[0] = rho0 * c0;
+  out[1] = rho0 * s0;
+  out[2] = rho1 * c1;
+  out[3] = rho1 * s1;
+}
+
+// W at one cell (used where a line does not start on a group boundary).
+template <typename R> __device__ __forceinline__ R noise_cell(uint64_t seed, uint64_t idx) {
+  R v[4];
+  gauss4(noise_words(seed, idx >> 2), v);
+  const int lane = (int)(idx & 3);
+  return lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : v[3];
+}
+
+// ------------------------------------------------------------------ butterflies
+// In-register DFT of length RAD: y_k = sum_n x_n exp(-+2 pi i n k / RAD)
+// (minus sign forward, plus sign for INV).
+template <int RAD, bool INV, typename T> struct Butterfly;
+
+template <bool INV, typename T> struct Butterfly<2, INV, T> {
+  static __device__ __forceinline__ void run(T *v) {
+    const T a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV, typename T> struct Butterfly<3, INV, T> {
+  static __device__ __forceinline__ void run(T *v) {
+    using R = decltype(v[0].x);
+    const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+    const T s = cadd(v[1], v[2]);
+    const T d = csub(v[1], v[2]);
+    const T t = {v[0].x - (R)0.5 * s.x, v[0].y - (R)0.5 * s.y};
+    const T hd = {h * d.x, h * d.y};
+    v[0] = cadd(v[0], s);
+    v[1] = cadd(t, mul_wi<INV>(hd));
+    v[2] = csub(t, mul_wi<INV>(hd));
+  }
+};
+
+template <bool INV, typename T> struct Butterfly<4, INV, T> {
+  static __device__ __forceinline__ void run(T *v) {
+    const T t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const T t2 = cadd(v[1], v[3]), t3 = mul_wi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <bool INV, typename T> struct Butterfly<8, INV, T> {
+  static __device__ __forceinline__ void run(T *v) {
+    using R = decltype(v[0].x);
+    const R r2 = (R)0.70710678118654752440;  // 1/sqrt(2)
+    T e[4] = {v[0], v[2], v[4], v[6]};
+    T o[4] = {v[1], v[3], v[5], v[7]};
+    Butterfly<4, INV, T>::run(e);
+    Butterfly<4, INV, T>::run(o);
+    // o_k *= w8^k, w8 = exp(-+2 pi i / 8)
+    T o1, o3;
+    if (INV) {
+      o1 = {r2 * (o[1].x - o[1].y), r2 * (o[1].x + o[1].y)};
+      o3 = {-r2 * (o[3].x + o[3].y), r2 * (o[3].x - o[3].y)};
+    } else {
+      o1 = {r2 * (o[1].x + o[1].y), r2 * (o[1].y - o[1].x)};
+      o3 = {r2 * (o[3].y - o[3].x), -r2 * (o[3].x + o[3].y)};
+    }
+    const T o2 = mul_wi<INV>(o[2]);
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+// ---------------------------------------------------------------- smem layouts
+// Contiguous lines (z passes): element n of line l at l * ld + n + n / 16.
+struct LineLayout {
+  int ld;
+  __device__ __forceinline__ int operator()(int l, int n) const { return l * ld + n + (n >> 4); }
+};
+// Column tiles (strided passes): point n of column c at n * cols + c.
+struct ColLayout {
+  int cols;
+  __device__ __forceinline__ int operator()(int c, int n) const {
+    const int o = n * cols + c;
+    return o + (o >> 5);
+  }
+};
+
+__host__ __device__ inline int line_ld(int half_len) { return half_len + (half_len >> 4) + 1; }
+__host__ __device__ inline int col_words(int len, int cols) {
+  const int o = len * cols;
+  return o + (o >> 5) + 1;
+}
+
+// One Stockham decimation-in-time stage on the line `l` of a tile in shared
+// memory. The CTA's threads each own butterflies j = p + P*b; every element is
+// read by one thread and written by one thread, so the stage runs in place
+// with a barrier between the reads and the writes.
+template <typename R, int E, int RAD, bool INV, class Lay>
+__device__ __forceinline__ void fft_stage(Cx<R> *buf, const Lay &lay, int l, int p, int P, int len,
+                                          int ns, int ns_shift, int tstep,
+                                          const Cx<R> *__restrict__ tw) {
+  constexpr int NB = E / RAD;
+  Cx<R> v[E];
+  const int span = len / RAD;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = p + P * b;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b * RAD + r] = buf[lay(l, j + r * span)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = p + P * b;
+    const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
+    if (ns > 1) {
+      const int t1 = k * tstep;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const Cx<R> w = ldg_c(tw + t1 * r);
+        v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
+      }
+    }
+    Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
+    const int base = (j - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) buf[lay(l, base + r * ns)] = v[b * RAD + r];
+  }
+  __syncthreads();
+}
+
+// All stages of st on line l (every thread of the CTA must call this).
+template <typename R, int E, bool INV, class Lay>
+__device__ __forceinline__ void fft_smem(Cx<R> *buf, const Lay &lay, int l, int p, int P,
+                                         const FftStages &st, const Cx<R> *__restrict__ tw) {
+  for (int s = 0; s < st.nstages; ++s) {
+    const int rad = st.radix[s];
+    const int ns = st.ns[s], sh = st.ns_shift[s], ts = st.tstep[s];
+    if constexpr (E % 8 == 0) {
+      if (rad == 8) { fft_stage<R, E, 8, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
+    }
+    if constexpr (E % 4 == 0) {
+      if (rad == 4) { fft_stage<R, E, 4, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
+    }
+    if constexpr (E % 2 == 0) {
+      if (rad == 2) { fft_stage<R, E, 2, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
+    }
+    if constexpr (E % 3 == 0) {
+      if (rad == 3) { fft_stage<R, E, 3, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
+    }
+  }
+}
+
+}  // namespace gg

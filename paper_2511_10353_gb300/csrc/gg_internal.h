@@ -1,0 +1,108 @@
+// Internal interface between the host runtime (gg_api.cpp, gg_cosmo.cpp) and
+// the sm_103a kernels (gg_kernels_*.cu). Plain C++: no device code here.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace gg {
+
+constexpr int kMaxStages = 16;
+
+// Radix schedule of one complex transform of length `len` done inside a CTA
+// (Stockham autosort, decimation in time). Stage s combines radix[s] partial
+// transforms of length ns[s]; every thread holds `e` elements of its line and
+// runs e / radix[s] butterflies per stage.
+struct FftStages {
+  int len;
+  int nstages;
+  int e;                      // elements per thread: a multiple of every radix
+  int radix[kMaxStages];
+  int ns[kMaxStages];         // product of the radices of earlier stages
+  int ns_shift[kMaxStages];   // log2(ns) when ns is a power of two, else -1
+  int tstep[kMaxStages];      // len / (ns * radix): twiddle index step
+};
+
+// Builds the schedule for len = 2^a 3^b (radix 8 first, then 4 / 2, then 3).
+bool make_stages(int len, FftStages *st);
+
+// Filters applied inside the strided (x) pass.
+enum Filter : int {
+  kFiltNone = 0,
+  kFiltDelta = 1,  // after the forward x transform: multiply by S_delta(m^2)
+  kFiltPsi = 2,    // before the inverse x transform: multiply delta~ by i m_j G(m^2)
+};
+
+// Forward z pass: real lines of N (generated noise or caller noise) -> half
+// spectra of N/2 complex (the z-Nyquist term is not kept).
+struct ZFwdArgs {
+  const void *noise;      // N^3 reals or nullptr: generate from seed
+  void *out;              // nlines * (N/2) complex
+  uint64_t seed;
+  int64_t nlines;         // N^2
+  int n;                  // N
+  int lines_per_cta;
+  FftStages st;           // length N/2
+  const void *tw_half;    // exp(-2 pi i t / (N/2)), t < N/2
+  const void *tw_full;    // exp(-2 pi i t / N), t < N
+};
+
+// Strided complex pass along y (axis 1) or x (axis 0) of the half spectrum
+// [N][N][N/2]. A CTA transforms `cols` adjacent kz columns of one outer index.
+struct ColArgs {
+  const void *src;
+  void *dst;              // may equal src
+  int64_t stride;         // complex elements between points along the axis
+  int64_t outer_stride;   // complex elements between outer indices
+  int inner_chunks;       // (N/2) / cols
+  int cols;
+  int n;                  // N
+  int axis;               // 0: x pass (outer index = ky), 1: y pass (outer = x)
+  FftStages st;           // length N
+  const void *tw;         // exp(-2 pi i t / N)
+  int filter;             // Filter
+  int comp;               // psi component for kFiltPsi
+  const void *table;      // S_delta (kFiltDelta) or G (kFiltPsi), indexed by m^2
+};
+
+// Inverse z pass (c2r) with the Zel'dovich epilogue (Eq. 3) or a plain real
+// output (density).
+struct ZInvArgs {
+  const void *src;        // nlines * (N/2) complex
+  void *psi;              // N^3 reals or nullptr
+  void *pos;
+  void *vel;
+  int64_t nlines;
+  int n;
+  int lines_per_cta;
+  int comp;               // 0, 1, 2: axis of the component (lattice coordinate)
+  double box;
+  double cell;            // L / N
+  double q_offset;        // 0.5 (cell centres) or 0 (corners)
+  double vfac;
+  FftStages st;           // length N/2
+  const void *tw_half;
+  const void *tw_full;
+};
+
+struct NoiseArgs {
+  void *out;              // N^3 reals
+  uint64_t seed;
+  int64_t cells;
+};
+
+template <typename R> cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s);
+template <typename R> cudaError_t launch_zfwd(const ZFwdArgs &a, cudaStream_t s);
+template <typename R> cudaError_t launch_col(const ColArgs &a, bool inverse, cudaStream_t s);
+template <typename R> cudaError_t launch_zinv(const ZInvArgs &a, cudaStream_t s);
+template <typename R> int max_block_threads(int kind, int e);
+cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint32_t *out,
+                              cudaStream_t s);
+
+// Shared-memory bytes of one CTA of each pass (the host sizes tiles with these).
+size_t zpass_smem_bytes(int half_len, int lines, size_t complex_bytes);
+size_t col_smem_bytes(int len, int cols, size_t complex_bytes);
+
+}  // namespace gg

@@ -1,0 +1,335 @@
+// Kernels of the noise -> Zel'dovich path (Secs. 2.1-2.2, Eqs. 1-3) and their
+// launchers. Included once per real type by gg_kernels_f32.cu / _f64.cu.
+//
+// Data layout in HBM: the half spectrum [N][N][N/2] complex (x, y, kz with kz
+// fastest) overlays exactly one real N^3 grid: the z-Nyquist plane is never
+// stored because the filter zeroes it (every mode with |m_j| = N/2 is dropped).
+#pragma once
+
+#include "gg_device.cuh"
+
+namespace gg {
+
+// ------------------------------------------------------------------ noise
+template <typename R>
+__global__ void k_noise(NoiseArgs a) {
+  const int64_t groups = (a.cells + 3) >> 2;
+  R *out = reinterpret_cast<R *>(a.out);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    R v[4];
+    gauss4(noise_words(a.seed, (uint64_t)g), v);
+    const int64_t c = g << 2;
+    if (c + 3 < a.cells) {
+      if constexpr (sizeof(R) == 4) {
+        *reinterpret_cast<float4 *>(out + c) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+        *reinterpret_cast<double2 *>(out + c) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(out + c + 2) = make_double2(v[2], v[3]);
+      }
+    } else {
+      for (int i = 0; i < 4 && c + i < a.cells; ++i) out[c + i] = v[i];
+    }
+  }
+}
+
+
+// ---------------------------------------------------------- forward z pass
+// One CTA: `lines_per_cta` z-lines. Each line of N reals (noise made in place
+// from (seed, cell index), or read) is packed as N/2 complex values
+// z_n = W_2n + i W_2n+1, transformed with the length-N/2 FFT and unpacked into
+// X_k = (Z_k + conj Z_{M-k})/2 - i/2 e^{-2 pi i k/N} (Z_k - conj Z_{M-k}),
+// k < N/2 (the real-input DFT).
+template <typename R, int E>
+__global__ void k_zfwd(const ZFwdArgs a) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int M = a.st.len, P = M / E;
+  const LineLayout lay{line_ld(M)};
+  const int l = threadIdx.x / P, p = threadIdx.x - l * P;
+  const int64_t line = (int64_t)blockIdx.x * a.lines_per_cta + l;
+  const bool live = line < a.nlines;
+  if (live) {
+    if (a.noise) {
+      const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
+#pragma unroll
+      for (int i = 0; i < E; ++i) buf[lay(l, p + P * i)] = src[p + P * i];
+    } else if ((a.n & 3) == 0) {
+      if constexpr (E % 2 == 0) {
+        const uint64_t g0 = (uint64_t)line * (uint64_t)(a.n >> 2);
+#pragma unroll
+        for (int i = 0; i < E / 2; ++i) {
+          const int q = p + P * i;
+          R v[4];
+          gauss4(noise_words(a.seed, g0 + q), v);
+          buf[lay(l, 2 * q)] = C{v[0], v[1]};
+          buf[lay(l, 2 * q + 1)] = C{v[2], v[3]};
+        }
+      }
+    } else {
+      const uint64_t c0 = (uint64_t)line * (uint64_t)a.n;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int k = p + P * i;
+        buf[lay(l, k)] = C{noise_cell<R>(a.seed, c0 + 2 * k), noise_cell<R>(a.seed, c0 + 2 * k + 1)};
+      }
+    }
+  }
+  __syncthreads();
+  fft_smem<R, E, false>(buf, lay, l, p, P, a.st, reinterpret_cast<const C *>(a.tw_half));
+  if (live) {
+    C *dst = reinterpret_cast<C *>(a.out) + line * M;
+    const C *twf = reinterpret_cast<const C *>(a.tw_full);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int k = p + P * i;
+      const C zk = buf[lay(l, k)];
+      const C zm = buf[lay(l, k ? M - k : 0)];
+      const C fe = {(R)0.5 * (zk.x + zm.x), (R)0.5 * (zk.y - zm.y)};
+      const C fo = {(R)0.5 * (zk.y + zm.y), (R)-0.5 * (zk.x - zm.x)};
+      dst[k] = cadd(fe, cmul(fo, ldg_c(twf + k)));
+    }
+  }
+}
+
+// ------------------------------------------------------- strided passes
+// One CTA: `cols` adjacent kz columns of one outer index, the whole axis of N
+// points. Optional filters: Eq. 1 after the forward x transform (S_delta(m^2),
+// which also carries the N^-3/2 transform factor and zeroes k = 0), Eq. 2
+// before the inverse x transform (i m_j G(m^2) with G = L / (2 pi m^2)).
+// Modes with m_x or m_y = -N/2 are zeroed by both filters.
+template <typename R>
+__device__ __forceinline__ Cx<R> apply_filter(const ColArgs &a, Cx<R> v, int n, int64_t outer,
+                                              int kz) {
+  const int N = a.n, half = N >> 1;
+  const int oy = (int)outer;
+  const int mx = n < half ? n : n - N;
+  const int my = oy < half ? oy : oy - N;
+  const int m2 = mx * mx + my * my + kz * kz;
+  const bool nyq = (n == half) || (oy == half);
+  const R *tab = reinterpret_cast<const R *>(a.table);
+  if (a.filter == kFiltDelta) {
+    const R s = nyq ? (R)0 : __ldg(tab + m2);
+    return Cx<R>{s * v.x, s * v.y};
+  }
+  const int mj = a.comp == 0 ? mx : (a.comp == 1 ? my : kz);
+  const R f = nyq ? (R)0 : (R)mj * __ldg(tab + m2);
+  return Cx<R>{-f * v.y, f * v.x};
+}
+
+template <typename R, int E, bool INV>
+__global__ void k_col(const ColArgs a) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int N = a.n, P = N / E, B = a.cols;
+  const ColLayout lay{B};
+  const int c = threadIdx.x & (B - 1), p = threadIdx.x / B;
+  const int64_t g = blockIdx.x;
+  const int64_t outer = g / a.inner_chunks;
+  const int chunk = (int)(g - outer * a.inner_chunks);
+  const int kz = chunk * B + c;
+  const int64_t base = outer * a.outer_stride + kz;
+  const C *src = reinterpret_cast<const C *>(a.src) + base;
+  C *dst = reinterpret_cast<C *>(a.dst) + base;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int n = p + P * i;
+    C v = src[(int64_t)n * a.stride];
+    if (a.filter == kFiltPsi) v = apply_filter<R>(a, v, n, outer, kz);
+    buf[lay(c, n)] = v;
+  }
+  __syncthreads();
+  fft_smem<R, E, INV>(buf, lay, c, p, P, a.st, reinterpret_cast<const C *>(a.tw));
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int n = p + P * i;
+    C v = buf[lay(c, n)];
+    if (a.filter == kFiltDelta) v = apply_filter<R>(a, v, n, outer, kz);
+    dst[(int64_t)n * a.stride] = v;
+  }
+}
+
+// ---------------------------------------------- inverse z pass + epilogue
+// c2r of each half-spectrum line (X_{N/2} = 0): Z_k = (X_k + conj X_{M-k})
+// + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), inverse FFT of length M = N/2,
+// x_2n = Re z_n, x_2n+1 = Im z_n. Then Eq. 3 per cell: psi, pos = (q + psi)
+// mod L, vel = vfac psi; or the plain real field when pos and vel are null.
+template <typename R>
+__device__ __forceinline__ R wrap_box(R x, R box) {
+  if (x < (R)0) x += box;
+  else if (x >= box) x -= box;
+  if (!(x >= (R)0 && x < box)) {
+    x = x - box * floor(x / box);
+    if (x >= box) x -= box;
+    if (x < (R)0) x = (R)0;
+  }
+  return x;
+}
+
+template <typename R, int E>
+__global__ void k_zinv(const ZInvArgs a) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int M = a.st.len, P = M / E;
+  const LineLayout lay{line_ld(M)};
+  const int l = threadIdx.x / P, p = threadIdx.x - l * P;
+  const int64_t line = (int64_t)blockIdx.x * a.lines_per_cta + l;
+  const bool live = line < a.nlines;
+  if (live) {
+    const C *src = reinterpret_cast<const C *>(a.src) + line * M;
+#pragma unroll
+    for (int i = 0; i < E; ++i) buf[lay(l, p + P * i)] = src[p + P * i];
+  }
+  __syncthreads();
+  C z[E];
+  const C *twf = reinterpret_cast<const C *>(a.tw_full);
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int k = p + P * i;
+    const C xk = buf[lay(l, k)];
+    const C xm = k ? buf[lay(l, M - k)] : C{(R)0, (R)0};
+    const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
+    const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
+    z[i] = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < E; ++i) buf[lay(l, p + P * i)] = z[i];
+  __syncthreads();
+  fft_smem<R, E, true>(buf, lay, l, p, P, a.st, reinterpret_cast<const C *>(a.tw_half));
+  if (!live) return;
+  const int64_t ix = line / a.n, iy = line - ix * a.n;
+  const R box = (R)a.box, cell = (R)a.cell, qo = (R)a.q_offset, vfac = (R)a.vfac;
+  const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
+  C *psi = a.psi ? reinterpret_cast<C *>(a.psi) + line * M : nullptr;
+  C *pos = a.pos ? reinterpret_cast<C *>(a.pos) + line * M : nullptr;
+  C *vel = a.vel ? reinterpret_cast<C *>(a.vel) + line * M : nullptr;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int n = p + P * i;
+    const C v = buf[lay(l, n)];
+    if (psi) psi[n] = v;
+    if (pos) {
+      R q0 = qline, q1 = qline;
+      if (a.comp == 2) {
+        q0 = ((R)(2 * n) + qo) * cell;
+        q1 = ((R)(2 * n + 1) + qo) * cell;
+      }
+      pos[n] = C{wrap_box<R>(q0 + v.x, box), wrap_box<R>(q1 + v.y, box)};
+    }
+    if (vel) vel[n] = C{vfac * v.x, vfac * v.y};
+  }
+}
+
+// ----------------------------------------------------------------- launchers
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define GG_DISPATCH_E(E_, ...)                 \
+  switch (E_) {                                 \
+    case 2: { constexpr int EE = 2; __VA_ARGS__; } break;  \
+    case 3: { constexpr int EE = 3; __VA_ARGS__; } break;  \
+    case 4: { constexpr int EE = 4; __VA_ARGS__; } break;  \
+    case 6: { constexpr int EE = 6; __VA_ARGS__; } break;  \
+    case 8: { constexpr int EE = 8; __VA_ARGS__; } break;  \
+    case 12: { constexpr int EE = 12; __VA_ARGS__; } break; \
+    case 24: { constexpr int EE = 24; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;      \
+  }
+
+template <typename R>
+cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s) {
+  const int64_t groups = (a.cells + 3) >> 2;
+  if (groups == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256;
+  int64_t blocks = (groups + threads - 1) / threads;
+  const int64_t cap = (int64_t)sms * 8;
+  if (blocks > cap) blocks = cap;
+  k_noise<R><<<(unsigned)blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
+  const int P = a.st.len / a.st.e;
+  const size_t smem = zpass_smem_bytes(a.st.len, a.lines_per_cta, sizeof(Cx<R>));
+  const unsigned blocks = (unsigned)((a.nlines + a.lines_per_cta - 1) / a.lines_per_cta);
+  const unsigned threads = (unsigned)(P * a.lines_per_cta);
+  GG_DISPATCH_E(a.st.e, {
+    auto kern = k_zfwd<R, EE>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, threads, smem, s>>>(a);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_col(const ColArgs &a, bool inverse, cudaStream_t s) {
+  const int P = a.n / a.st.e;
+  const size_t smem = col_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
+  const int64_t outer = a.n;  // N outer indices in both passes
+  const unsigned blocks = (unsigned)(outer * a.inner_chunks);
+  const unsigned threads = (unsigned)(P * a.cols);
+  GG_DISPATCH_E(a.st.e, {
+    if (inverse) {
+      auto kern = k_col<R, EE, true>;
+      cudaError_t e = set_smem(kern, smem);
+      if (e != cudaSuccess) return e;
+      kern<<<blocks, threads, smem, s>>>(a);
+    } else {
+      auto kern = k_col<R, EE, false>;
+      cudaError_t e = set_smem(kern, smem);
+      if (e != cudaSuccess) return e;
+      kern<<<blocks, threads, smem, s>>>(a);
+    }
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_zinv(const ZInvArgs &a, cudaStream_t s) {
+  const int P = a.st.len / a.st.e;
+  const size_t smem = zpass_smem_bytes(a.st.len, a.lines_per_cta, sizeof(Cx<R>));
+  const unsigned blocks = (unsigned)((a.nlines + a.lines_per_cta - 1) / a.lines_per_cta);
+  const unsigned threads = (unsigned)(P * a.lines_per_cta);
+  GG_DISPATCH_E(a.st.e, {
+    auto kern = k_zinv<R, EE>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, threads, smem, s>>>(a);
+  });
+  return cudaGetLastError();
+}
+
+// Largest block each kernel can launch with (registers bound it), so the host
+// can size tiles: kind 0 = forward z, 1 = strided, 2 = inverse z.
+template <typename R>
+int max_block_threads(int kind, int e) {
+  cudaFuncAttributes fa{};
+  cudaError_t err = cudaErrorInvalidValue;
+  GG_DISPATCH_E(e, {
+    if (kind == 0) err = cudaFuncGetAttributes(&fa, k_zfwd<R, EE>);
+    else if (kind == 1) err = cudaFuncGetAttributes(&fa, k_col<R, EE, false>);
+    else err = cudaFuncGetAttributes(&fa, k_zinv<R, EE>);
+  });
+  return err == cudaSuccess ? fa.maxThreadsPerBlock : -1;
+}
+
+#define GG_INSTANTIATE(R)                                                         \
+  template cudaError_t launch_noise<R>(const NoiseArgs &, cudaStream_t);          \
+  template cudaError_t launch_zfwd<R>(const ZFwdArgs &, cudaStream_t);            \
+  template cudaError_t launch_col<R>(const ColArgs &, bool, cudaStream_t);        \
+  template cudaError_t launch_zinv<R>(const ZInvArgs &, cudaStream_t);          \
+  template int max_block_threads<R>(int, int);
+
+}  // namespace gg
