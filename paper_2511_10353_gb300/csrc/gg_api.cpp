@@ -53,6 +53,7 @@ struct gg_plan {
   int *err = nullptr;     // device error word
   gg::FftStages st_n{}, st_half{};
   int z_lines = 1, col_b = 1;
+  int col_e = 1, col_rows_box = 0;  // strided passes: elements per thread, TMA box height
   std::string last_error;
   // host-buffer entry point: device staging of two components, a copy stream
   void *stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -230,7 +231,31 @@ void choose_tiles(gg_plan_t *plan) {
     while (lines > 1 && (P * lines > cap || gg::zpass_smem_bytes(half, lines, cb) > smem_cap)) lines /= 2;
     plan->z_lines = lines;
   }
-  // strided passes: up to 16 adjacent columns, at most 512 threads
+  // strided passes, TMA path: rows of 128 bytes (64 when two tiles would not
+  // fit in shared memory), at most 512 threads, elements per thread doubled
+  // from the radix minimum until the CTA fits
+  plan->col_e = plan->st_n.e;
+  plan->col_rows_box = 0;
+  if (sizeof(R) == 8 || half % 2 == 0) {
+    int b = (int)(128 / cb);
+    while (b > 1 && half % b != 0) b /= 2;
+    while (b > 1 && gg::colt_smem_bytes(n, b, cb) > 200 * 1024) b /= 2;
+    int e = plan->st_n.e;
+    while ((n / e) * b > 512 && n % (2 * e) == 0 && 2 * e <= 24 && 2 * e != 48) e *= 2;
+    const int cap = gg::max_block_threads<R>(3, e);
+    while (b > 1 && (n / e) * b > std::min(cap > 0 ? cap : 512, 512)) b /= 2;
+    if ((size_t)b * cb >= 16 && (n / e) * b <= 1024 && (e == 2 || e == 3 || e == 4 || e == 6 ||
+        e == 8 || e == 12 || e == 16 || e == 24)) {
+      int rows = 1;
+      for (int d = 1; d <= 256 && d <= n; ++d)
+        if (n % d == 0) rows = d;
+      plan->col_b = b;
+      plan->col_e = e;
+      plan->col_rows_box = rows;
+      return;
+    }
+  }
+  // fallback (odd N/2 in FP32): one tile per CTA, up to 16 columns, <= 512 threads
   {
     const int P = n / plan->st_n.e;
     int cap = gg::max_block_threads<R>(1, plan->st_n.e);
@@ -320,6 +345,9 @@ gg_status forward_passes(gg_plan_t *plan, uint64_t seed, const void *noise) {
   c.n = n;
   c.st = plan->st_n;
   c.tw = plan->tab.tw_n;
+  c.e = plan->col_e;
+  c.rows_box = plan->col_rows_box;
+  c.err = plan->err;
   // y pass: points stride N/2, outer index x with stride N * N/2
   c.axis = 1;
   c.stride = half;
@@ -358,6 +386,9 @@ gg_status inverse_passes(gg_plan_t *plan, int comp, void *scratch, void *psi, vo
   c.n = n;
   c.st = plan->st_n;
   c.tw = plan->tab.tw_n;
+  c.e = plan->col_e;
+  c.rows_box = plan->col_rows_box;
+  c.err = plan->err;
   c.axis = 0;
   c.stride = (int64_t)n * half;
   c.outer_stride = half;

@@ -228,6 +228,120 @@ __device__ __forceinline__ void fft_stage(Cx<R> *buf, const Lay &lay, int l, int
   __syncthreads();
 }
 
+// ------------------------------------------------ TMA and mbarrier helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's (and, after a CTA barrier, the CTA's) generic-proxy
+// shared-memory accesses before later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity. Returns false (and sets
+// *err = 2) when the budget of polls runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+  for (uint32_t i = 0; i < (1u << 24); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, 2);
+  return false;
+}
+// 3-D tiled TMA load global -> shared, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+// Plain bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// One Stockham stage with caller-supplied element access: ld(n) returns
+// element n of the stage input, st(n, v) stores element n of its output. With
+// SYNC the stage runs in place in shared memory (barrier between all reads
+// and all writes, and after the writes).
+template <typename R, int E, int RAD, bool INV, bool SYNC, class Ld, class St>
+__device__ __forceinline__ void stage_io(int p, int P, int len, int ns, int ns_shift, int tstep,
+                                         const Cx<R> *__restrict__ tw, const Ld &ld, const St &st) {
+  constexpr int NB = E / RAD;
+  Cx<R> v[E];
+  const int span = len / RAD;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = p + P * b;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b * RAD + r] = ld(j + r * span);
+  }
+  if (SYNC) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = p + P * b;
+    const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
+    if (ns > 1) {
+      const int t1 = k * tstep;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const Cx<R> w = ldg_c(tw + t1 * r);
+        v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
+      }
+    }
+    Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
+    const int base = (j - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) st(base + r * ns, v[b * RAD + r]);
+  }
+  if (SYNC) __syncthreads();
+}
+
+// Runs stage s of st with the radix dispatched at run time.
+template <typename R, int E, bool INV, bool SYNC, class Ld, class St>
+__device__ __forceinline__ void stage_dispatch(const FftStages &st, int s, int p, int P,
+                                               const Cx<R> *__restrict__ tw, const Ld &ld,
+                                               const St &sto) {
+  const int rad = st.radix[s], ns = st.ns[s], sh = st.ns_shift[s], ts = st.tstep[s];
+  if constexpr (E % 8 == 0) {
+    if (rad == 8) { stage_io<R, E, 8, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
+  }
+  if constexpr (E % 4 == 0) {
+    if (rad == 4) { stage_io<R, E, 4, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
+  }
+  if constexpr (E % 2 == 0) {
+    if (rad == 2) { stage_io<R, E, 2, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
+  }
+  if constexpr (E % 3 == 0) {
+    if (rad == 3) { stage_io<R, E, 3, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
+  }
+}
+
 // All stages of st on line l (every thread of the CTA must call this).
 template <typename R, int E, bool INV, class Lay>
 __device__ __forceinline__ void fft_smem(Cx<R> *buf, const Lay &lay, int l, int p, int P,

@@ -65,6 +65,9 @@ struct ColArgs {
   int filter;             // Filter
   int comp;               // psi component for kFiltPsi
   const void *table;      // S_delta (kFiltDelta) or G (kFiltPsi), indexed by m^2
+  int e;                  // elements per thread (multiple of st.e)
+  int rows_box;           // TMA box height (a divisor of N, <= 256); 0: no TMA
+  int *err;               // device error word
 };
 
 // Inverse z pass (c2r) with the Zel'dovich epilogue (Eq. 3) or a plain real
@@ -104,5 +107,6 @@ cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint3
 // Shared-memory bytes of one CTA of each pass (the host sizes tiles with these).
 size_t zpass_smem_bytes(int half_len, int lines, size_t complex_bytes);
 size_t col_smem_bytes(int len, int cols, size_t complex_bytes);
+size_t colt_smem_bytes(int len, int cols, size_t complex_bytes);
 
 }  // namespace gg

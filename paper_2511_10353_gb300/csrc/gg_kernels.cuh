@@ -6,6 +6,9 @@
 // stored because the filter zeroes it (every mode with |m_j| = N/2 is dropped).
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "gg_device.cuh"
 
 namespace gg {
@@ -151,6 +154,90 @@ __global__ void k_col(const ColArgs a) {
   }
 }
 
+// Persistent, double-buffered variant of the strided pass. Each CTA walks the
+// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread issues the TMA
+// loads of tile t+1 (3-D tensor map over [x][y][kz], box of `cols` kz columns
+// by rows_box points) into the second shared buffer while the CTA transforms
+// tile t. The first FFT stage reads the TMA buffer (applying the Eq. 2 filter
+// when asked); intermediate stages run in place in shared memory; the last
+// stage writes straight to HBM (applying the Eq. 1 filter when asked). Rows
+// of `cols` complex values are 64 or 128 bytes, so every half-warp (FP32) or
+// quarter-warp (FP64) access covers whole rows.
+template <typename R, int E, bool INV>
+__global__ void __launch_bounds__(512, 1) k_colt(const __grid_constant__ CUtensorMap map,
+                                                 const ColArgs a) {
+  using C = Cx<R>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  const int N = a.n, P = N / E, B = a.cols;
+  const int tile_elems = N * B;
+  const int stride_elems = ((tile_elems * (int)sizeof(C) + 127) & ~127) / (int)sizeof(C);
+  C *bufs = reinterpret_cast<C *>(smem_raw + 128);
+  const int tid = threadIdx.x;
+  const int c = tid & (B - 1), p = tid / B;
+  const int64_t ntiles = (int64_t)N * a.inner_chunks;
+  const uint32_t tile_bytes = (uint32_t)(tile_elems * sizeof(C));
+  const C *tw = reinterpret_cast<const C *>(a.tw);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t t, int s) {
+    const int64_t outer = t / a.inner_chunks;
+    const int chunk = (int)(t - outer * a.inner_chunks);
+    C *dst = bufs + s * stride_elems;
+    mbar_arrive_expect_tx(&bars[s], tile_bytes);
+    const int c0 = chunk * B * 2;  // innermost coordinate in reals
+    for (int i = 0; i < N; i += a.rows_box) {
+      if (a.axis == 1) tma_load_3d(dst + i * B, &map, &bars[s], c0, i, (int)outer);
+      else tma_load_3d(dst + i * B, &map, &bars[s], c0, (int)outer, i);
+    }
+  };
+  int64_t t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    const int64_t tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {
+      fence_proxy_async_smem();
+      issue(tn, s ^ 1);
+    }
+    const bool ok = __syncthreads_and(mbar_wait(&bars[s], (uint32_t)((it >> 1) & 1), a.err));
+    if (!ok) {
+      if (tid == 0 && tn < ntiles) mbar_wait(&bars[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+      return;
+    }
+    C *buf = bufs + s * stride_elems;
+    const int64_t outer = t / a.inner_chunks;
+    const int chunk = (int)(t - outer * a.inner_chunks);
+    const int kz = chunk * B + c;
+    C *dst = reinterpret_cast<C *>(a.dst) + outer * a.outer_stride + kz;
+    const int S = a.st.nstages;
+    auto ld_first = [&](int n) {
+      C v = buf[n * B + c];
+      if (a.filter == kFiltPsi) v = apply_filter<R>(a, v, n, outer, kz);
+      return v;
+    };
+    auto ld_smem = [&](int n) { return buf[n * B + c]; };
+    auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
+    auto st_glob = [&](int n, C v) {
+      if (a.filter == kFiltDelta) v = apply_filter<R>(a, v, n, outer, kz);
+      dst[(int64_t)n * a.stride] = v;
+    };
+    if (S == 1) {
+      stage_dispatch<R, E, INV, false>(a.st, 0, p, P, tw, ld_first, st_glob);
+    } else {
+      stage_dispatch<R, E, INV, true>(a.st, 0, p, P, tw, ld_first, st_smem);
+      for (int si = 1; si < S - 1; ++si)
+        stage_dispatch<R, E, INV, true>(a.st, si, p, P, tw, ld_smem, st_smem);
+      stage_dispatch<R, E, INV, false>(a.st, S - 1, p, P, tw, ld_smem, st_glob);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------- inverse z pass + epilogue
 // c2r of each half-spectrum line (X_{N/2} = 0): Z_k = (X_k + conj X_{M-k})
 // + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), inverse FFT of length M = N/2,
@@ -239,6 +326,7 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     case 6: { constexpr int EE = 6; __VA_ARGS__; } break;  \
     case 8: { constexpr int EE = 8; __VA_ARGS__; } break;  \
     case 12: { constexpr int EE = 12; __VA_ARGS__; } break; \
+    case 16: { constexpr int EE = 16; __VA_ARGS__; } break; \
     case 24: { constexpr int EE = 24; __VA_ARGS__; } break; \
     default: return cudaErrorInvalidValue;      \
   }
@@ -273,11 +361,84 @@ cudaError_t launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+static EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+// Tensor map of the half spectrum [N][N][N/2] complex as reals (innermost
+// 2 * N/2 reals), with a box of `cols` complex columns by rows_box points
+// along the pass axis.
+template <typename R>
+static cudaError_t make_map(CUtensorMap *m, const ColArgs &a) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t half = (cuuint64_t)(a.n / 2);
+  cuuint64_t dims[3] = {2 * half, (cuuint64_t)a.n, (cuuint64_t)a.n};
+  cuuint64_t strides[2] = {2 * half * sizeof(R), (cuuint64_t)a.n * 2 * half * sizeof(R)};
+  cuuint32_t box[3];
+  box[0] = (cuuint32_t)(2 * a.cols);
+  box[1] = a.axis == 1 ? (cuuint32_t)a.rows_box : 1u;
+  box[2] = a.axis == 1 ? 1u : (cuuint32_t)a.rows_box;
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r =
+      fn(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+         const_cast<void *>(a.src), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t colt_smem_bytes(int len, int cols, size_t complex_bytes);
+
+template <typename K>
+static int persistent_blocks(K kernel, int threads, size_t smem, int64_t tiles) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  const int64_t b = (int64_t)sms * per;
+  return (int)(tiles < b ? tiles : b);
+}
+
 template <typename R>
 cudaError_t launch_col(const ColArgs &a, bool inverse, cudaStream_t s) {
+  const int64_t outer = a.n;  // N outer indices in both passes
+  if (a.rows_box > 0) {
+    CUtensorMap map;
+    cudaError_t e = make_map<R>(&map, a);
+    if (e != cudaSuccess) return e;
+    const int P = a.n / a.e;
+    const unsigned threads = (unsigned)(P * a.cols);
+    const size_t smem = colt_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
+    const int64_t tiles = outer * a.inner_chunks;
+    GG_DISPATCH_E(a.e, {
+      if (inverse) {
+        auto kern = k_colt<R, EE, true>;
+        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+        kern<<<persistent_blocks(kern, threads, smem, tiles), threads, smem, s>>>(map, a);
+      } else {
+        auto kern = k_colt<R, EE, false>;
+        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+        kern<<<persistent_blocks(kern, threads, smem, tiles), threads, smem, s>>>(map, a);
+      }
+    });
+    return cudaGetLastError();
+  }
   const int P = a.n / a.st.e;
   const size_t smem = col_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
-  const int64_t outer = a.n;  // N outer indices in both passes
   const unsigned blocks = (unsigned)(outer * a.inner_chunks);
   const unsigned threads = (unsigned)(P * a.cols);
   GG_DISPATCH_E(a.st.e, {
@@ -320,6 +481,7 @@ int max_block_threads(int kind, int e) {
   GG_DISPATCH_E(e, {
     if (kind == 0) err = cudaFuncGetAttributes(&fa, k_zfwd<R, EE>);
     else if (kind == 1) err = cudaFuncGetAttributes(&fa, k_col<R, EE, false>);
+    else if (kind == 3) err = cudaFuncGetAttributes(&fa, k_colt<R, EE, false>);
     else err = cudaFuncGetAttributes(&fa, k_zinv<R, EE>);
   });
   return err == cudaSuccess ? fa.maxThreadsPerBlock : -1;
