@@ -1,16 +1,17 @@
 // C ABI of the Zel'dovich initial-conditions path (include/gg.h): parameter
 // validation, FP64 tables, workspace ownership and the pass schedule.
 //
-// Pass schedule of gg_zeldovich ("one component at a time", Sec. 2.1: the
-// memory for the three velocity-field components is a little over two grids):
-//   z  forward  (noise generated in registers -> half spectrum)   write 4 B/cell
-//   y  forward                                                    r+w 8 B/cell
-//   x  forward  + Eq. 1 filter -> delta~ (kept)                   r+w 8 B/cell
-//   for j in x, y, z:
-//     x inverse with Eq. 2 applied on load (delta~ -> scratch)    r+w 8 B/cell
-//     y inverse                                                   r+w 8 B/cell
-//     z inverse (c2r) + Eq. 3 epilogue -> psi_j / pos_j / vel_j   r 4 + w 4 per output
-// (FP32 byte counts; FP64 doubles them.)
+// Pass schedule of gg_zeldovich (FP32 bytes per cell; FP64 doubles them):
+//   z forward   noise made in registers -> half spectrum W~          write 4
+//   y forward   W~ along y                                          r+w 8
+//   x fused     forward x, then per output: filter, inverse x       read 4, write 4 per output
+//                 A = X^-1[i m_x U W~]  (-> psi_x)
+//                 B = X^-1[U W~]        (-> psi_y, psi_z)
+//               with U = D sqrt(P/V) N^-3/2 (L / 2 pi) / m^2 (Eqs. 1-2)
+//   y inverse   A -> Y^-1 A;  B -> Y^-1[i m_y B], Y^-1 B            read 4, write 4 per output
+//   z inverse   c2r (i m_z applied on load for psi_z) + Eq. 3       read 4, write 4 per output
+// i m_y and i m_z commute with the x (and y) transforms, so psi_y and psi_z
+// share B: 80 B/cell for positions + velocities.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -34,8 +35,8 @@ thread_local std::string g_thread_error;
 struct Tables {
   void *tw_n = nullptr;     // length N: exp(-2 pi i t / N)
   void *tw_half = nullptr;  // length N/2
-  void *s_delta = nullptr;  // 3 (N/2)^2 + 1 entries
-  void *g_psi = nullptr;    // 3 (N/2)^2 + 1 entries
+  void *s_delta = nullptr;  // S(m2) N^-3/2, 3 (N/2)^2 + 1 entries (density filter, Eq. 1)
+  void *u_phi = nullptr;    // S(m2) N^-3/2 (L / 2 pi) / m2 (potential; psi~_j = i m_j U W~)
 };
 
 }  // namespace
@@ -47,11 +48,12 @@ struct gg_plan {
   cudaStream_t stream = nullptr;
   size_t real_bytes = 0;  // sizeof(R)
   int64_t cells = 0;      // N^3
-  void *work = nullptr;   // N^3 reals: half spectrum, delta~ after the forward passes
-  void *work2 = nullptr;  // N^3 reals: per-component inverse transforms
+  void *work = nullptr;   // N^3 reals: half spectrum; the psi_x branch after the x pass
+  void *work2 = nullptr;  // N^3 reals, allocated on first use: the psi_y branch
+  void *work3 = nullptr;  // N^3 reals, allocated on first use: the psi_z branch
   Tables tab;
   int *err = nullptr;     // device error word
-  gg::FftStages st_n{}, st_half{};
+  gg::FftStages st_n{}, st_n_inv{}, st_half{};
   int z_lines = 1, col_b = 1;
   int col_e = 1, col_rows_box = 0;  // strided passes: elements per thread, TMA box height
   std::string last_error;
@@ -162,7 +164,7 @@ size_t table_entries(int64_t n) { return (size_t)(3 * (n / 2) * (n / 2) + 1); }
 size_t workspace_bytes(const gg_params *p) {
   const size_t rb = p->prec == GG_F64 ? 8 : 4;
   const size_t grid = (size_t)p->n * p->n * p->n * rb;
-  return 2 * grid + (size_t)(p->n + p->n / 2) * 2 * rb + 2 * table_entries(p->n) * rb + 256;
+  return 3 * grid + (size_t)(p->n + p->n / 2) * 2 * rb + 2 * table_entries(p->n) * rb + 256;
 }
 
 template <typename R>
@@ -207,13 +209,13 @@ gg_status build_tables(gg_plan_t *plan, const gg::cosmo::Model &m) {
   std::vector<double> s(cnt);
   filter_values(&plan->p, m, plan->info.growth, s.data(), (int64_t)cnt);
   const double norm = 1.0 / std::pow((double)n, 1.5);  // orthonormal forward transform
-  std::vector<R> sd(cnt), gp(cnt);
+  std::vector<R> sd(cnt), up(cnt);
   for (size_t i = 0; i < cnt; ++i) {
     sd[i] = (R)(s[i] * norm);
-    gp[i] = i ? (R)(plan->p.box / (2.0 * kPi * (double)i)) : (R)0;  // (L / 2 pi) / m2
+    up[i] = i ? (R)(s[i] * norm * plan->p.box / (2.0 * kPi * (double)i)) : (R)0;
   }
   if ((st = upload(plan, &plan->tab.s_delta, sd)) != GG_OK) return st;
-  return upload(plan, &plan->tab.g_psi, gp);
+  return upload(plan, &plan->tab.u_phi, up);
 }
 
 template <typename R>
@@ -224,53 +226,37 @@ void choose_tiles(gg_plan_t *plan) {
   // z passes: about 256 threads per CTA
   {
     const int P = half / plan->st_half.e;
-    int cap = std::min(gg::max_block_threads<R>(0, plan->st_half.e),
-                       gg::max_block_threads<R>(2, plan->st_half.e));
+    int cap = std::min(gg::max_block_threads_z<R>(0, plan->st_half.e),
+                       gg::max_block_threads_z<R>(2, plan->st_half.e));
     if (cap <= 0) cap = 256;
     int lines = std::max(1, 256 / P);
     while (lines > 1 && (P * lines > cap || gg::zpass_smem_bytes(half, lines, cb) > smem_cap)) lines /= 2;
     plan->z_lines = lines;
   }
-  // strided passes, TMA path: rows of 128 bytes (64 when two tiles would not
-  // fit in shared memory), at most 512 threads, elements per thread doubled
-  // from the radix minimum until the CTA fits
-  plan->col_e = plan->st_n.e;
-  plan->col_rows_box = 0;
-  if (sizeof(R) == 8 || half % 2 == 0) {
-    int b = (int)(128 / cb);
-    while (b > 1 && half % b != 0) b /= 2;
-    while (b > 1 && gg::colt_smem_bytes(n, b, cb) > 200 * 1024) b /= 2;
-    int e = plan->st_n.e;
-    while ((n / e) * b > 512 && n % (2 * e) == 0 && 2 * e <= 24 && 2 * e != 48) e *= 2;
-    const int cap = gg::max_block_threads<R>(3, e);
-    while (b > 1 && (n / e) * b > std::min(cap > 0 ? cap : 512, 512)) b /= 2;
-    if ((size_t)b * cb >= 16 && (n / e) * b <= 1024 && (e == 2 || e == 3 || e == 4 || e == 6 ||
-        e == 8 || e == 12 || e == 16 || e == 24)) {
-      int rows = 1;
-      for (int d = 1; d <= 256 && d <= n; ++d)
-        if (n % d == 0) rows = d;
-      plan->col_b = b;
-      plan->col_e = e;
-      plan->col_rows_box = rows;
-      return;
-    }
-  }
-  // fallback (odd N/2 in FP32): one tile per CTA, up to 16 columns, <= 512 threads
-  {
-    const int P = n / plan->st_n.e;
-    int cap = gg::max_block_threads<R>(1, plan->st_n.e);
-    if (cap <= 0) cap = 256;
-    cap = std::min(cap, 512);
-    int b = 16;
-    while (b > 1 && (half % b != 0 || P * b > cap || gg::col_smem_bytes(n, b, cb) > smem_cap)) b /= 2;
-    plan->col_b = b;
-  }
+  // strided passes: rows of up to 128 bytes, halved while two tiles would not
+  // fit in shared memory or the CTA would exceed 512 threads (or what the
+  // kernel's registers allow); TMA unless FP32 rows of N/2 complex values are
+  // not a multiple of 16 bytes (odd N/2)
+  int b = (int)(128 / cb);
+  while (b > 1 && half % b != 0) b /= 2;
+  while (b > 1 && gg::axis_smem_bytes(n, b, cb) > 200 * 1024) b /= 2;
+  const int e = plan->st_n.e;
+  int cap = gg::max_block_threads_axis<R>(e);
+  if (cap <= 0) cap = 256;
+  while (b > 1 && (n / e) * b > std::min(cap, 512)) b /= 2;
+  int rows = 1;
+  for (int d = 1; d <= 256 && d <= n; ++d)
+    if (n % d == 0) rows = d;
+  plan->col_b = b;
+  plan->col_e = e;
+  plan->col_rows_box = (sizeof(R) == 8 || half % 2 == 0) && (size_t)b * cb >= 16 ? rows : 0;
 }
 
 void release(gg_plan_t *plan) {
   if (!plan) return;
-  void *bufs[] = {plan->work, plan->work2, plan->tab.tw_n, plan->tab.tw_half, plan->tab.s_delta,
-                  plan->tab.g_psi, plan->err, plan->noise_stage};
+  void *bufs[] = {plan->work,        plan->work2,         plan->work3,
+                  plan->tab.tw_n,    plan->tab.tw_half,   plan->tab.s_delta,
+                  plan->tab.u_phi,   plan->err,           plan->noise_stage};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (auto &slot : plan->stage)
@@ -290,10 +276,9 @@ void release(gg_plan_t *plan) {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // ------------------------------------------------------------ kernel timing
-enum Kind { kZFwd = 0, kYFwd, kXFwd, kXInv, kYInv, kZInv, kNoise, kNumKinds };
-const char *const kKindNames[kNumKinds] = {"z_forward_noise", "y_forward", "x_forward_filter",
-                                           "x_inverse_filter", "y_inverse", "z_inverse_epilogue",
-                                           "noise"};
+enum Kind { kZFwd = 0, kYFwd, kXFused, kYInv, kZInv, kNoise, kNumKinds };
+const char *const kKindNames[kNumKinds] = {"z_forward_noise", "y_forward", "x_fused_filter",
+                                           "y_inverse", "z_inverse_epilogue", "noise"};
 
 // Records a start event before a launch and an end event after it when the
 // plan's profiling is on; `bytes` is the launch's algorithmic HBM traffic.
@@ -319,8 +304,41 @@ struct ProfScope {
 
 // ----------------------------------------------------------- pass launchers
 template <typename R>
-gg_status forward_passes(gg_plan_t *plan, uint64_t seed, const void *noise) {
+gg::AxisArgs axis_args(gg_plan_t *plan, int axis, const void *src) {
   const int n = (int)plan->p.n, half = n / 2;
+  gg::AxisArgs c{};
+  c.src = src;
+  c.cols = plan->col_b;
+  c.inner_chunks = half / plan->col_b;
+  c.n = n;
+  c.axis = axis;
+  c.stride = axis == 1 ? half : (int64_t)n * half;
+  c.outer_stride = axis == 1 ? (int64_t)n * half : half;
+  c.st_fwd = plan->st_n;
+  c.st_inv = plan->st_n_inv;
+  c.tw = plan->tab.tw_n;
+  c.e = plan->col_e;
+  c.rows_box = plan->col_rows_box;
+  c.err = plan->err;
+  return c;
+}
+
+template <typename R>
+gg_status launch_axis_timed(gg_plan_t *plan, const gg::AxisArgs &c, int kind, const char *what) {
+  const double cb = (double)plan->cells * sizeof(R);
+  const double bytes = (c.fwd && !c.inv ? 2 : 1 + c.nout) * cb;
+  cudaError_t e;
+  {
+    ProfScope ps(plan, kind, bytes);
+    e = gg::launch_axis<R>(c, plan->stream);
+  }
+  return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, what);
+}
+
+// z forward (noise or caller noise) and y forward into plan->work.
+template <typename R>
+gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
+  const int n = (int)plan->p.n;
   gg::ZFwdArgs z{};
   z.noise = noise;
   z.out = plan->work;
@@ -338,89 +356,29 @@ gg_status forward_passes(gg_plan_t *plan, uint64_t seed, const void *noise) {
     e = gg::launch_zfwd<R>(z, plan->stream);
   }
   if (e != cudaSuccess) return cuda_fail(plan, e, "z forward pass");
-  gg::ColArgs c{};
-  c.src = c.dst = plan->work;
-  c.cols = plan->col_b;
-  c.inner_chunks = half / plan->col_b;
-  c.n = n;
-  c.st = plan->st_n;
-  c.tw = plan->tab.tw_n;
-  c.e = plan->col_e;
-  c.rows_box = plan->col_rows_box;
-  c.err = plan->err;
-  // y pass: points stride N/2, outer index x with stride N * N/2
-  c.axis = 1;
-  c.stride = half;
-  c.outer_stride = (int64_t)n * half;
-  c.filter = gg::kFiltNone;
-  {
-    ProfScope ps(plan, kYFwd, 2 * cb);
-    e = gg::launch_col<R>(c, false, plan->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(plan, e, "y forward pass");
-  // x pass + Eq. 1: points stride N * N/2, outer index ky with stride N/2
-  c.axis = 0;
-  c.stride = (int64_t)n * half;
-  c.outer_stride = half;
-  c.filter = gg::kFiltDelta;
-  c.table = plan->tab.s_delta;
-  {
-    ProfScope ps(plan, kXFwd, 2 * cb);
-    e = gg::launch_col<R>(c, false, plan->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(plan, e, "x forward pass");
-  return GG_OK;
+  gg::AxisArgs c = axis_args<R>(plan, 1, plan->work);
+  c.fwd = 1;
+  c.inv = 0;
+  c.nout = 1;
+  c.dst[0] = plan->work;
+  c.mul[0] = gg::kMulNone;
+  return launch_axis_timed<R>(plan, c, kYFwd, "y forward pass");
 }
 
-// delta~ in plan->work -> inverse x (optional Eq. 2 filter) into `scratch`,
-// inverse y, inverse z with the epilogue.
 template <typename R>
-gg_status inverse_passes(gg_plan_t *plan, int comp, void *scratch, void *psi, void *pos,
-                         void *vel) {
-  const int n = (int)plan->p.n, half = n / 2;
-  gg::ColArgs c{};
-  c.src = plan->work;
-  c.dst = scratch;
-  c.cols = plan->col_b;
-  c.inner_chunks = half / plan->col_b;
-  c.n = n;
-  c.st = plan->st_n;
-  c.tw = plan->tab.tw_n;
-  c.e = plan->col_e;
-  c.rows_box = plan->col_rows_box;
-  c.err = plan->err;
-  c.axis = 0;
-  c.stride = (int64_t)n * half;
-  c.outer_stride = half;
-  c.filter = comp >= 0 ? gg::kFiltPsi : gg::kFiltNone;
-  c.comp = comp;
-  c.table = plan->tab.g_psi;
-  const double cb = (double)plan->cells * sizeof(R);
-  cudaError_t e;
-  {
-    ProfScope ps(plan, kXInv, 2 * cb);
-    e = gg::launch_col<R>(c, true, plan->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(plan, e, "x inverse pass");
-  c.src = c.dst = scratch;
-  c.axis = 1;
-  c.stride = half;
-  c.outer_stride = (int64_t)n * half;
-  c.filter = gg::kFiltNone;
-  {
-    ProfScope ps(plan, kYInv, 2 * cb);
-    e = gg::launch_col<R>(c, true, plan->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(plan, e, "y inverse pass");
+gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void *pos, void *vel,
+                    bool mul_kz) {
+  const int n = (int)plan->p.n;
   gg::ZInvArgs z{};
-  z.src = scratch;
+  z.src = src;
   z.psi = psi;
   z.pos = pos;
   z.vel = vel;
   z.nlines = (int64_t)n * n;
   z.n = n;
   z.lines_per_cta = plan->z_lines;
-  z.comp = comp < 0 ? 0 : comp;
+  z.comp = comp;
+  z.mul_kz = mul_kz ? 1 : 0;
   z.box = plan->p.box;
   z.cell = plan->p.box / (double)n;
   z.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
@@ -428,30 +386,130 @@ gg_status inverse_passes(gg_plan_t *plan, int comp, void *scratch, void *psi, vo
   z.st = plan->st_half;
   z.tw_half = plan->tab.tw_half;
   z.tw_full = plan->tab.tw_n;
+  const double cb = (double)plan->cells * sizeof(R);
+  const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
+  cudaError_t e;
   {
-    const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
     ProfScope ps(plan, kZInv, (1 + outs) * cb);
     e = gg::launch_zinv<R>(z, plan->stream);
   }
-  if (e != cudaSuccess) return cuda_fail(plan, e, "z inverse pass");
+  return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, "z inverse pass");
+}
+
+gg_status ensure_grid(gg_plan_t *plan, void **buf) {
+  if (*buf) return GG_OK;
+  if (cudaMalloc(buf, (size_t)plan->cells * plan->real_bytes) != cudaSuccess) {
+    *buf = nullptr;
+    return fail(plan, GG_ENOMEM, "cudaMalloc of a component workspace failed");
+  }
+  return GG_OK;
+}
+
+// Everything up to the inverse z passes. On return src[j] holds, for each
+// wanted component j, the half-spectrum lines whose c2r (times i m_z for
+// j = 2) is psi_j. psi_dev[1] / psi_dev[2], when given, serve as the buffers
+// of the y / z branches (the z pass then writes psi in place).
+template <typename R>
+gg_status spectral_passes(gg_plan_t *plan, uint64_t seed, const void *noise, const bool want[3],
+                          void *const psi_dev[3], void *src[3]) {
+  gg_status st = forward_zy<R>(plan, seed, noise);
+  if (st != GG_OK) return st;
+  void *buf_y = nullptr, *buf_z = nullptr;
+  if (want[1]) {
+    buf_y = (psi_dev && psi_dev[1]) ? psi_dev[1] : nullptr;
+    if (!buf_y && (st = ensure_grid(plan, &plan->work2)) != GG_OK) return st;
+    if (!buf_y) buf_y = plan->work2;
+  }
+  if (want[2]) {
+    buf_z = (psi_dev && psi_dev[2]) ? psi_dev[2] : nullptr;
+    if (!buf_z && (st = ensure_grid(plan, &plan->work3)) != GG_OK) return st;
+    if (!buf_z) buf_z = plan->work3;
+  }
+  // x fused: A -> work (in place), B -> the y buffer (or the z buffer)
+  void *buf_b = want[1] ? buf_y : buf_z;
+  gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
+  x.fwd = 1;
+  x.inv = 1;
+  x.pre = 1;
+  x.table = plan->tab.u_phi;
+  x.nout = 0;
+  if (want[0]) {
+    x.dst[x.nout] = plan->work;
+    x.mul[x.nout++] = gg::kMulIm;
+  }
+  if (want[1] || want[2]) {
+    x.dst[x.nout] = buf_b;
+    x.mul[x.nout++] = gg::kMulNone;
+  }
+  if ((st = launch_axis_timed<R>(plan, x, kXFused, "x fused pass")) != GG_OK) return st;
+  if (want[0]) {
+    gg::AxisArgs y = axis_args<R>(plan, 1, plan->work);
+    y.inv = 1;
+    y.nout = 1;
+    y.dst[0] = plan->work;
+    y.mul[0] = gg::kMulNone;
+    if ((st = launch_axis_timed<R>(plan, y, kYInv, "y inverse pass (x branch)")) != GG_OK) return st;
+  }
+  if (want[1] || want[2]) {
+    gg::AxisArgs y = axis_args<R>(plan, 1, buf_b);
+    y.inv = 1;
+    y.nout = 0;
+    if (want[1]) {
+      y.dst[y.nout] = buf_y;
+      y.mul[y.nout++] = gg::kMulIm;
+    }
+    if (want[2]) {
+      y.dst[y.nout] = buf_z;
+      y.mul[y.nout++] = gg::kMulNone;
+    }
+    if ((st = launch_axis_timed<R>(plan, y, kYInv, "y inverse pass (y/z branches)")) != GG_OK)
+      return st;
+  }
+  src[0] = want[0] ? plan->work : nullptr;
+  src[1] = buf_y;
+  src[2] = buf_z;
   return GG_OK;
 }
 
 template <typename R>
 gg_status run_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise, void *const psi[3],
                         void *const pos[3], void *const vel[3]) {
-  gg_status st = forward_passes<R>(plan, seed, noise);
+  bool want[3];
+  for (int j = 0; j < 3; ++j)
+    want[j] = (psi && psi[j]) || (pos && pos[j]) || (vel && vel[j]);
+  if (!want[0] && !want[1] && !want[2]) return GG_OK;
+  void *src[3];
+  gg_status st = spectral_passes<R>(plan, seed, noise, want, psi, src);
   if (st != GG_OK) return st;
   for (int j = 0; j < 3; ++j) {
-    void *ps = psi ? psi[j] : nullptr, *po = pos ? pos[j] : nullptr, *ve = vel ? vel[j] : nullptr;
-    if (!ps && !po && !ve) continue;
-    // the psi buffer doubles as the scratch of its own component (the inverse
-    // z pass reads each line into shared memory before writing it back)
-    void *scratch = ps ? ps : plan->work2;
-    st = inverse_passes<R>(plan, j, scratch, ps, po, ve);
+    if (!want[j]) continue;
+    st = zinv_pass<R>(plan, j, src[j], psi ? psi[j] : nullptr, pos ? pos[j] : nullptr,
+                      vel ? vel[j] : nullptr, j == 2);
     if (st != GG_OK) return st;
   }
   return GG_OK;
+}
+
+template <typename R>
+gg_status run_density(gg_plan_t *plan, uint64_t seed, const void *noise, void *delta) {
+  gg_status st = forward_zy<R>(plan, seed, noise);
+  if (st != GG_OK) return st;
+  gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
+  x.fwd = 1;
+  x.inv = 1;
+  x.pre = 1;
+  x.table = plan->tab.s_delta;
+  x.nout = 1;
+  x.dst[0] = plan->work;
+  x.mul[0] = gg::kMulNone;
+  if ((st = launch_axis_timed<R>(plan, x, kXFused, "x fused pass")) != GG_OK) return st;
+  gg::AxisArgs y = axis_args<R>(plan, 1, plan->work);
+  y.inv = 1;
+  y.nout = 1;
+  y.dst[0] = plan->work;
+  y.mul[0] = gg::kMulNone;
+  if ((st = launch_axis_timed<R>(plan, y, kYInv, "y inverse pass")) != GG_OK) return st;
+  return zinv_pass<R>(plan, 0, plan->work, delta, nullptr, nullptr, false);
 }
 
 template <typename R>
@@ -460,13 +518,12 @@ gg_status create(gg_plan_t *plan, const gg::cosmo::Model &m) {
   const int64_t n = plan->p.n;
   if (!gg::make_stages((int)n, &plan->st_n) || !gg::make_stages((int)(n / 2), &plan->st_half))
     return fail(plan, GG_EINVAL, "no FFT schedule for this n");
+  plan->st_n_inv = gg::reversed_stages(plan->st_n);
   gg_status st = build_tables<R>(plan, m);
   if (st != GG_OK) return st;
   const size_t grid = (size_t)plan->cells * sizeof(R);
   if (cudaMalloc(&plan->work, grid) != cudaSuccess)
     return fail(plan, GG_ENOMEM, "cudaMalloc of the transform workspace failed");
-  if (cudaMalloc(&plan->work2, grid) != cudaSuccess)
-    return fail(plan, GG_ENOMEM, "cudaMalloc of the component workspace failed");
   if (cudaMalloc(&plan->err, 256) != cudaSuccess)
     return fail(plan, GG_ENOMEM, "cudaMalloc of the error word failed");
   cudaError_t e = cudaMemset(plan->err, 0, 256);
@@ -490,6 +547,10 @@ gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void 
         return cuda_fail(plan, e, "cudaEventCreate");
     }
   }
+  bool want[3];
+  for (int j = 0; j < 3; ++j)
+    want[j] = (psi && psi[j]) || (pos && pos[j]) || (vel && vel[j]);
+  if (!want[0] && !want[1] && !want[2]) return GG_OK;
   const void *noise_dev = nullptr;
   if (noise_host) {
     if (!plan->noise_stage && cudaMalloc(&plan->noise_stage, grid) != cudaSuccess)
@@ -499,13 +560,16 @@ gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void 
       return cuda_fail(plan, e, "noise upload");
     noise_dev = plan->noise_stage;
   }
-  gg_status st = forward_passes<R>(plan, seed, noise_dev);
+  void *src[3];
+  gg_status st = spectral_passes<R>(plan, seed, noise_dev, want, nullptr, src);
   if (st != GG_OK) return st;
+  // inverse z per component into a staging slot; its download overlaps the
+  // next component's z pass
   bool used[2] = {false, false};
+  int slot = 0;
   for (int j = 0; j < 3; ++j) {
+    if (!want[j]) continue;
     void *hs[3] = {psi ? psi[j] : nullptr, pos ? pos[j] : nullptr, vel ? vel[j] : nullptr};
-    if (!hs[0] && !hs[1] && !hs[2]) continue;
-    const int slot = j & 1;
     for (int o = 0; o < 3; ++o)
       if (hs[o] && !plan->stage[slot][o] && cudaMalloc(&plan->stage[slot][o], grid) != cudaSuccess)
         return fail(plan, GG_ENOMEM, "cudaMalloc of an output staging buffer failed");
@@ -513,8 +577,7 @@ gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void 
       return cuda_fail(plan, e, "cudaStreamWaitEvent");
     void *dv[3] = {hs[0] ? plan->stage[slot][0] : nullptr, hs[1] ? plan->stage[slot][1] : nullptr,
                    hs[2] ? plan->stage[slot][2] : nullptr};
-    void *scratch = dv[0] ? dv[0] : plan->work2;
-    st = inverse_passes<R>(plan, j, scratch, dv[0], dv[1], dv[2]);
+    st = zinv_pass<R>(plan, j, src[j], dv[0], dv[1], dv[2], j == 2);
     if (st != GG_OK) return st;
     if ((e = cudaEventRecord(plan->ev_comp[slot], plan->stream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(plan->copy_stream, plan->ev_comp[slot], 0)) != cudaSuccess)
@@ -526,6 +589,7 @@ gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void 
     if ((e = cudaEventRecord(plan->ev_copy[slot], plan->copy_stream)) != cudaSuccess)
       return cuda_fail(plan, e, "cudaEventRecord");
     used[slot] = true;
+    slot ^= 1;
   }
   if ((e = cudaStreamSynchronize(plan->copy_stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(plan->stream)) != cudaSuccess)
@@ -564,6 +628,24 @@ bool make_stages(int len, FftStages *st) {
     ns *= rad[s];
   }
   return true;
+}
+
+FftStages reversed_stages(const FftStages &f) {
+  FftStages st;
+  std::memset(&st, 0, sizeof(st));
+  st.len = f.len;
+  st.e = f.e;
+  st.nstages = f.nstages;
+  int ns = 1;
+  for (int s = 0; s < f.nstages; ++s) {
+    const int rad = f.radix[f.nstages - 1 - s];
+    st.radix[s] = rad;
+    st.ns[s] = ns;
+    st.ns_shift[s] = (ns & (ns - 1)) == 0 ? __builtin_ctz((unsigned)ns) : -1;
+    st.tstep[s] = f.len / (ns * rad);
+    ns *= rad;
+  }
+  return st;
 }
 
 }  // namespace gg
@@ -678,13 +760,8 @@ gg_status gg_gaussian_field(gg_plan_t *plan, uint64_t seed, const void *noise_de
   if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
   if (!delta_dev || !aligned16(delta_dev) || (noise_dev && !aligned16(noise_dev)))
     return fail(plan, GG_EINVAL, "delta_dev NULL or a buffer unaligned");
-  gg_status st = plan->real_bytes == 8 ? forward_passes<double>(plan, seed, noise_dev)
-                                       : forward_passes<float>(plan, seed, noise_dev);
-  if (st != GG_OK) return st;
-  // comp < 0: no Eq. 2 filter; the inverse runs in place on delta~
-  return plan->real_bytes == 8
-             ? inverse_passes<double>(plan, -1, plan->work, delta_dev, nullptr, nullptr)
-             : inverse_passes<float>(plan, -1, plan->work, delta_dev, nullptr, nullptr);
+  return plan->real_bytes == 8 ? run_density<double>(plan, seed, noise_dev, delta_dev)
+                               : run_density<float>(plan, seed, noise_dev, delta_dev);
 }
 
 gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,

@@ -1,0 +1,7 @@
+// F32 instantiation of the strided (y / x) passes.
+#define GG_AXIS_TU 1
+#include "gg_kernels.cuh"
+
+namespace gg {
+GG_INSTANTIATE_AXIS(float)
+}  // namespace gg

@@ -35,6 +35,8 @@ template <bool INV, typename T> __device__ __forceinline__ T mul_wi(T a) {
 
 template <typename T> __device__ __forceinline__ T ldg_c(const T *p) { return __ldg(p); }
 
+template <int V> struct IntC { static constexpr int value = V; };
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
 // (SC'11): ten rounds of the 4x32 Philox S-box/P-box with a Weyl key schedule.
@@ -175,58 +177,7 @@ struct LineLayout {
   int ld;
   __device__ __forceinline__ int operator()(int l, int n) const { return l * ld + n + (n >> 4); }
 };
-// Column tiles (strided passes): point n of column c at n * cols + c.
-struct ColLayout {
-  int cols;
-  __device__ __forceinline__ int operator()(int c, int n) const {
-    const int o = n * cols + c;
-    return o + (o >> 5);
-  }
-};
-
 __host__ __device__ inline int line_ld(int half_len) { return half_len + (half_len >> 4) + 1; }
-__host__ __device__ inline int col_words(int len, int cols) {
-  const int o = len * cols;
-  return o + (o >> 5) + 1;
-}
-
-// One Stockham decimation-in-time stage on the line `l` of a tile in shared
-// memory. The CTA's threads each own butterflies j = p + P*b; every element is
-// read by one thread and written by one thread, so the stage runs in place
-// with a barrier between the reads and the writes.
-template <typename R, int E, int RAD, bool INV, class Lay>
-__device__ __forceinline__ void fft_stage(Cx<R> *buf, const Lay &lay, int l, int p, int P, int len,
-                                          int ns, int ns_shift, int tstep,
-                                          const Cx<R> *__restrict__ tw) {
-  constexpr int NB = E / RAD;
-  Cx<R> v[E];
-  const int span = len / RAD;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int j = p + P * b;
-#pragma unroll
-    for (int r = 0; r < RAD; ++r) v[b * RAD + r] = buf[lay(l, j + r * span)];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int j = p + P * b;
-    const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
-    if (ns > 1) {
-      const int t1 = k * tstep;
-#pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        const Cx<R> w = ldg_c(tw + t1 * r);
-        v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
-      }
-    }
-    Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
-    const int base = (j - k) * RAD + k;
-#pragma unroll
-    for (int r = 0; r < RAD; ++r) buf[lay(l, base + r * ns)] = v[b * RAD + r];
-  }
-  __syncthreads();
-}
 
 // ------------------------------------------------ TMA and mbarrier helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -276,6 +227,9 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t
       "l"(map), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 // Plain bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile(
@@ -285,14 +239,109 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       : "memory");
 }
 
-// One Stockham stage with caller-supplied element access: ld(n) returns
-// element n of the stage input, st(n, v) stores element n of its output. With
-// SYNC the stage runs in place in shared memory (barrier between all reads
-// and all writes, and after the writes).
+// ------------------------------------------------------------- Stockham stage
+// Multiplies v[r] (r = 1 .. RAD-1) by w^r (conjugated for INV), the powers
+// formed from w = w^1 by at most three products (FP32, where a table load
+// costs more than four FMAs) or read from the table (FP64, whose arithmetic
+// is the scarce resource on this GPU).
+template <int RAD, bool INV, typename T>
+__device__ __forceinline__ void twiddle_powers(T *v, T w1) {
+  auto mul = [](T x, T w) { return INV ? cmulc(x, w) : cmul(x, w); };
+  if constexpr (RAD == 2) {
+    v[1] = mul(v[1], w1);
+  } else if constexpr (RAD == 3) {
+    const T w2 = cmul(w1, w1);
+    v[1] = mul(v[1], w1);
+    v[2] = mul(v[2], w2);
+  } else if constexpr (RAD == 4) {
+    const T w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+    v[1] = mul(v[1], w1);
+    v[2] = mul(v[2], w2);
+    v[3] = mul(v[3], w3);
+  } else {
+    const T w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
+    const T w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+    v[1] = mul(v[1], w1);
+    v[2] = mul(v[2], w2);
+    v[3] = mul(v[3], w3);
+    v[4] = mul(v[4], w4);
+    v[5] = mul(v[5], w5);
+    v[6] = mul(v[6], w6);
+    v[7] = mul(v[7], w7);
+  }
+}
+
+// Twiddles of one stage for this thread's butterflies j = p + P*b (FP32):
+// w^1 per butterfly, loaded before the stage's shared-memory reads so that the
+// load latency overlaps them. FP64 reads each power from the table at use:
+// FP64 arithmetic, not load latency, is the scarce resource on this GPU.
+template <typename R, int E, int RAD> struct StageTw {
+  static constexpr int kCount = sizeof(R) == 4 ? E / RAD : 1;
+  Cx<R> w[kCount];
+};
+
+template <typename R, int E, int RAD>
+__device__ __forceinline__ void load_twiddles(StageTw<R, E, RAD> &t, int p, int P, int ns,
+                                              int ns_shift, int tstep, const Cx<R> *__restrict__ tw) {
+  if constexpr (sizeof(R) == 4) {
+    if (ns <= 1) return;
+#pragma unroll
+    for (int b = 0; b < E / RAD; ++b) {
+      const int j = p + P * b;
+      const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
+      t.w[b] = ldg_c(tw + k * tstep);
+    }
+  }
+}
+
+// Butterflies of one Stockham decimation-in-time stage on registers: v holds,
+// for each butterfly j = p + P*b of this thread, the RAD inputs at positions
+// j + r*len/RAD; on return it holds the outputs for positions
+// (j - k)*RAD + k + r*ns, k = j mod ns.
+template <typename R, int E, int RAD, bool INV>
+__device__ __forceinline__ void stage_compute(Cx<R> *v, int p, int P, int ns, int ns_shift, int tstep,
+                                              const StageTw<R, E, RAD> &t,
+                                              const Cx<R> *__restrict__ tw) {
+  constexpr int NB = E / RAD;
+  if (ns > 1) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if constexpr (sizeof(R) == 4) {
+        twiddle_powers<RAD, INV>(&v[b * RAD], t.w[b]);
+      } else {
+        const int j = p + P * b;
+        const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          const Cx<R> w = ldg_c(tw + k * tstep * r);
+          v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
+}
+
+// Output position of element r of butterfly j in a stage with ns.
+__device__ __forceinline__ int stage_out_pos(int j, int r, int ns, int ns_shift, int rad) {
+  const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
+  return (j - k) * rad + k + r * ns;
+}
+
+// One whole stage with caller-supplied element access: ld(n) returns element
+// n of the stage input, st(n, v) stores element n of its output. With SYNC the
+// stage runs in place in shared memory (barrier between all reads and all
+// writes, and after the writes).
 template <typename R, int E, int RAD, bool INV, bool SYNC, class Ld, class St>
 __device__ __forceinline__ void stage_io(int p, int P, int len, int ns, int ns_shift, int tstep,
                                          const Cx<R> *__restrict__ tw, const Ld &ld, const St &st) {
   constexpr int NB = E / RAD;
+  // opaque to the optimiser: keeps this stage's index arithmetic inside the
+  // stage instead of hoisted (and live) across the whole kernel
+  asm volatile("" : "+r"(p));
+  StageTw<R, E, RAD> t;
+  load_twiddles<R, E, RAD>(t, p, P, ns, ns_shift, tstep, tw);
   Cx<R> v[E];
   const int span = len / RAD;
 #pragma unroll
@@ -302,66 +351,52 @@ __device__ __forceinline__ void stage_io(int p, int P, int len, int ns, int ns_s
     for (int r = 0; r < RAD; ++r) v[b * RAD + r] = ld(j + r * span);
   }
   if (SYNC) __syncthreads();
+  stage_compute<R, E, RAD, INV>(v, p, P, ns, ns_shift, tstep, t, tw);
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = p + P * b;
-    const int k = ns_shift >= 0 ? (j & ((1 << ns_shift) - 1)) : (j % ns);
-    if (ns > 1) {
-      const int t1 = k * tstep;
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        const Cx<R> w = ldg_c(tw + t1 * r);
-        v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
-      }
-    }
-    Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
-    const int base = (j - k) * RAD + k;
-#pragma unroll
-    for (int r = 0; r < RAD; ++r) st(base + r * ns, v[b * RAD + r]);
+    for (int r = 0; r < RAD; ++r) st(stage_out_pos(j, r, ns, ns_shift, RAD), v[b * RAD + r]);
   }
   if (SYNC) __syncthreads();
 }
 
-// Runs stage s of st with the radix dispatched at run time.
+// Calls f(std::integral_constant<int, RAD>) for the run-time radix `rad`.
+template <int E, class F>
+__device__ __forceinline__ void with_radix(int rad, const F &f) {
+  if constexpr (E % 8 == 0) {
+    if (rad == 8) { f(IntC<8>{}); return; }
+  }
+  if constexpr (E % 4 == 0) {
+    if (rad == 4) { f(IntC<4>{}); return; }
+  }
+  if constexpr (E % 2 == 0) {
+    if (rad == 2) { f(IntC<2>{}); return; }
+  }
+  if constexpr (E % 3 == 0) {
+    if (rad == 3) { f(IntC<3>{}); return; }
+  }
+}
+
+// Stage s of st with the radix dispatched at run time.
 template <typename R, int E, bool INV, bool SYNC, class Ld, class St>
 __device__ __forceinline__ void stage_dispatch(const FftStages &st, int s, int p, int P,
                                                const Cx<R> *__restrict__ tw, const Ld &ld,
                                                const St &sto) {
-  const int rad = st.radix[s], ns = st.ns[s], sh = st.ns_shift[s], ts = st.tstep[s];
-  if constexpr (E % 8 == 0) {
-    if (rad == 8) { stage_io<R, E, 8, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
-  }
-  if constexpr (E % 4 == 0) {
-    if (rad == 4) { stage_io<R, E, 4, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
-  }
-  if constexpr (E % 2 == 0) {
-    if (rad == 2) { stage_io<R, E, 2, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
-  }
-  if constexpr (E % 3 == 0) {
-    if (rad == 3) { stage_io<R, E, 3, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto); return; }
-  }
+  const int ns = st.ns[s], sh = st.ns_shift[s], ts = st.tstep[s];
+  with_radix<E>(st.radix[s], [&](auto rc) {
+    stage_io<R, E, decltype(rc)::value, INV, SYNC>(p, P, st.len, ns, sh, ts, tw, ld, sto);
+  });
 }
 
-// All stages of st on line l (every thread of the CTA must call this).
+// All stages of st on line l of a LineLayout tile (every thread of the CTA
+// must call this).
 template <typename R, int E, bool INV, class Lay>
 __device__ __forceinline__ void fft_smem(Cx<R> *buf, const Lay &lay, int l, int p, int P,
                                          const FftStages &st, const Cx<R> *__restrict__ tw) {
-  for (int s = 0; s < st.nstages; ++s) {
-    const int rad = st.radix[s];
-    const int ns = st.ns[s], sh = st.ns_shift[s], ts = st.tstep[s];
-    if constexpr (E % 8 == 0) {
-      if (rad == 8) { fft_stage<R, E, 8, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
-    }
-    if constexpr (E % 4 == 0) {
-      if (rad == 4) { fft_stage<R, E, 4, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
-    }
-    if constexpr (E % 2 == 0) {
-      if (rad == 2) { fft_stage<R, E, 2, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
-    }
-    if constexpr (E % 3 == 0) {
-      if (rad == 3) { fft_stage<R, E, 3, INV>(buf, lay, l, p, P, st.len, ns, sh, ts, tw); continue; }
-    }
-  }
+  auto ld = [&](int n) { return buf[lay(l, n)]; };
+  auto sto = [&](int n, Cx<R> v) { buf[lay(l, n)] = v; };
+  for (int s = 0; s < st.nstages; ++s) stage_dispatch<R, E, INV, true>(st, s, p, P, tw, ld, sto);
 }
 
 }  // namespace gg

@@ -27,12 +27,46 @@ struct FftStages {
 
 // Builds the schedule for len = 2^a 3^b (radix 8 first, then 4 / 2, then 3).
 bool make_stages(int len, FftStages *st);
+// The same radices in reverse order (the inverse transforms start with the
+// radix the forward ones end with).
+FftStages reversed_stages(const FftStages &f);
 
-// Filters applied inside the strided (x) pass.
-enum Filter : int {
-  kFiltNone = 0,
-  kFiltDelta = 1,  // after the forward x transform: multiply by S_delta(m^2)
-  kFiltPsi = 2,    // before the inverse x transform: multiply delta~ by i m_j G(m^2)
+// Multipliers of the strided passes. The spectrum handed from the forward to
+// the inverse transforms is first multiplied by T(m2) when `pre` is set (x
+// pass only: m2 = m_x^2 + m_y^2 + m_z^2 with the outer index ky; modes with
+// m_x or m_y = -N/2 give 0), then each output by its own factor.
+enum Mul : int {
+  kMulNone = 0,  // v
+  kMulIm = 1,    // i m v, m = integer frequency along the pass axis (0 at -N/2)
+};
+
+// A strided pass over the half spectrum [N][N][N/2] complex along y (axis 1:
+// outer index x) or x (axis 0: outer index ky). A CTA owns `cols` adjacent kz
+// columns of one outer index, all N points. Modes:
+//   fwd && !inv : forward transform, write the spectrum (x T if pre) to dst[0]
+//   fwd &&  inv : forward transform, x T if pre, then for each output o:
+//                 x mul[o], inverse transform, write to dst[o]
+//  !fwd &&  inv : for each output o: x mul[o], inverse transform -> dst[o]
+struct AxisArgs {
+  const void *src;
+  void *dst[3];
+  int nout;
+  int mul[3];
+  int fwd, inv;
+  int64_t stride;         // complex elements between points along the axis
+  int64_t outer_stride;   // complex elements between outer indices
+  int inner_chunks;       // (N/2) / cols
+  int cols;
+  int n;                  // N
+  int axis;               // 0: x, 1: y
+  FftStages st_fwd;       // forward schedule (radix 8 first, 3 last)
+  FftStages st_inv;       // inverse schedule: the same radices in reverse order
+  const void *tw;         // exp(-2 pi i t / N)
+  int pre;                // 1: multiply the handed-off spectrum by table[m2]
+  const void *table;      // T(m2)
+  int e;                  // elements per thread (multiple of every radix)
+  int rows_box;           // TMA box height (divisor of N, <= 256); 0: plain loads
+  int *err;               // device error word
 };
 
 // Forward z pass: real lines of N (generated noise or caller noise) -> half
@@ -49,27 +83,6 @@ struct ZFwdArgs {
   const void *tw_full;    // exp(-2 pi i t / N), t < N
 };
 
-// Strided complex pass along y (axis 1) or x (axis 0) of the half spectrum
-// [N][N][N/2]. A CTA transforms `cols` adjacent kz columns of one outer index.
-struct ColArgs {
-  const void *src;
-  void *dst;              // may equal src
-  int64_t stride;         // complex elements between points along the axis
-  int64_t outer_stride;   // complex elements between outer indices
-  int inner_chunks;       // (N/2) / cols
-  int cols;
-  int n;                  // N
-  int axis;               // 0: x pass (outer index = ky), 1: y pass (outer = x)
-  FftStages st;           // length N
-  const void *tw;         // exp(-2 pi i t / N)
-  int filter;             // Filter
-  int comp;               // psi component for kFiltPsi
-  const void *table;      // S_delta (kFiltDelta) or G (kFiltPsi), indexed by m^2
-  int e;                  // elements per thread (multiple of st.e)
-  int rows_box;           // TMA box height (a divisor of N, <= 256); 0: no TMA
-  int *err;               // device error word
-};
-
 // Inverse z pass (c2r) with the Zel'dovich epilogue (Eq. 3) or a plain real
 // output (density).
 struct ZInvArgs {
@@ -81,6 +94,7 @@ struct ZInvArgs {
   int n;
   int lines_per_cta;
   int comp;               // 0, 1, 2: axis of the component (lattice coordinate)
+  int mul_kz;             // 1: multiply the half spectrum by i m_z before the c2r
   double box;
   double cell;            // L / N
   double q_offset;        // 0.5 (cell centres) or 0 (corners)
@@ -98,15 +112,15 @@ struct NoiseArgs {
 
 template <typename R> cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s);
 template <typename R> cudaError_t launch_zfwd(const ZFwdArgs &a, cudaStream_t s);
-template <typename R> cudaError_t launch_col(const ColArgs &a, bool inverse, cudaStream_t s);
+template <typename R> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t s);
 template <typename R> cudaError_t launch_zinv(const ZInvArgs &a, cudaStream_t s);
-template <typename R> int max_block_threads(int kind, int e);
+template <typename R> int max_block_threads_z(int kind, int e);  // kind 0: z forward, 2: z inverse
+template <typename R> int max_block_threads_axis(int e);
 cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint32_t *out,
                               cudaStream_t s);
 
 // Shared-memory bytes of one CTA of each pass (the host sizes tiles with these).
 size_t zpass_smem_bytes(int half_len, int lines, size_t complex_bytes);
-size_t col_smem_bytes(int len, int cols, size_t complex_bytes);
-size_t colt_smem_bytes(int len, int cols, size_t complex_bytes);
+size_t axis_smem_bytes(int len, int cols, size_t complex_bytes);
 
 }  // namespace gg

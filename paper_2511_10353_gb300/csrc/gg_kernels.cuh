@@ -6,6 +6,8 @@
 // stored because the filter zeroes it (every mode with |m_j| = N/2 is dropped).
 #pragma once
 
+#include <cstring>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -46,7 +48,7 @@ __global__ void k_noise(NoiseArgs a) {
 template <typename R, int E>
 __global__ void k_zfwd(const ZFwdArgs a) {
   using C = Cx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   const int M = a.st.len, P = M / E;
   const LineLayout lay{line_ld(M)};
@@ -97,142 +99,194 @@ __global__ void k_zfwd(const ZFwdArgs a) {
 }
 
 // ------------------------------------------------------- strided passes
-// One CTA: `cols` adjacent kz columns of one outer index, the whole axis of N
-// points. Optional filters: Eq. 1 after the forward x transform (S_delta(m^2),
-// which also carries the N^-3/2 transform factor and zeroes k = 0), Eq. 2
-// before the inverse x transform (i m_j G(m^2) with G = L / (2 pi m^2)).
-// Modes with m_x or m_y = -N/2 are zeroed by both filters.
+__device__ __forceinline__ int freq_of(int n, int N) { return n < (N >> 1) ? n : n - N; }
+
 template <typename R>
-__device__ __forceinline__ Cx<R> apply_filter(const ColArgs &a, Cx<R> v, int n, int64_t outer,
-                                              int kz) {
-  const int N = a.n, half = N >> 1;
-  const int oy = (int)outer;
-  const int mx = n < half ? n : n - N;
-  const int my = oy < half ? oy : oy - N;
-  const int m2 = mx * mx + my * my + kz * kz;
-  const bool nyq = (n == half) || (oy == half);
-  const R *tab = reinterpret_cast<const R *>(a.table);
-  if (a.filter == kFiltDelta) {
-    const R s = nyq ? (R)0 : __ldg(tab + m2);
-    return Cx<R>{s * v.x, s * v.y};
+__device__ __forceinline__ Cx<R> apply_mul(int kind, Cx<R> v, int n, int N) {
+  if (kind == kMulIm) {
+    const R f = n == (N >> 1) ? (R)0 : (R)freq_of(n, N);
+    return Cx<R>{-f * v.y, f * v.x};
   }
-  const int mj = a.comp == 0 ? mx : (a.comp == 1 ? my : kz);
-  const R f = nyq ? (R)0 : (R)mj * __ldg(tab + m2);
-  return Cx<R>{-f * v.y, f * v.x};
+  return v;
 }
 
-template <typename R, int E, bool INV>
-__global__ void k_col(const ColArgs a) {
-  using C = Cx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *buf = reinterpret_cast<C *>(smem_raw);
-  const int N = a.n, P = N / E, B = a.cols;
-  const ColLayout lay{B};
-  const int c = threadIdx.x & (B - 1), p = threadIdx.x / B;
-  const int64_t g = blockIdx.x;
-  const int64_t outer = g / a.inner_chunks;
-  const int chunk = (int)(g - outer * a.inner_chunks);
-  const int kz = chunk * B + c;
-  const int64_t base = outer * a.outer_stride + kz;
-  const C *src = reinterpret_cast<const C *>(a.src) + base;
-  C *dst = reinterpret_cast<C *>(a.dst) + base;
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int n = p + P * i;
-    C v = src[(int64_t)n * a.stride];
-    if (a.filter == kFiltPsi) v = apply_filter<R>(a, v, n, outer, kz);
-    buf[lay(c, n)] = v;
-  }
-  __syncthreads();
-  fft_smem<R, E, INV>(buf, lay, c, p, P, a.st, reinterpret_cast<const C *>(a.tw));
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int n = p + P * i;
-    C v = buf[lay(c, n)];
-    if (a.filter == kFiltDelta) v = apply_filter<R>(a, v, n, outer, kz);
-    dst[(int64_t)n * a.stride] = v;
-  }
-}
-
-// Persistent, double-buffered variant of the strided pass. Each CTA walks the
-// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread issues the TMA
-// loads of tile t+1 (3-D tensor map over [x][y][kz], box of `cols` kz columns
-// by rows_box points) into the second shared buffer while the CTA transforms
-// tile t. The first FFT stage reads the TMA buffer (applying the Eq. 2 filter
-// when asked); intermediate stages run in place in shared memory; the last
-// stage writes straight to HBM (applying the Eq. 1 filter when asked). Rows
-// of `cols` complex values are 64 or 128 bytes, so every half-warp (FP32) or
-// quarter-warp (FP64) access covers whole rows.
-template <typename R, int E, bool INV>
-__global__ void __launch_bounds__(512, 1) k_colt(const __grid_constant__ CUtensorMap map,
-                                                 const ColArgs a) {
+// Persistent strided pass (see AxisArgs). Each CTA walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread issues the TMA loads
+// of tile t+1 (3-D tensor map over [x][y][kz], box of `cols` kz columns by
+// rows_box points) into the second shared buffer while the CTA transforms
+// tile t. Forward stages run in place in shared memory except the last, whose
+// outputs stay in registers: they sit at the positions the first inverse stage
+// reads (same radix, inverse radices in reverse order), so the filter
+// multiplies registers and no shared round trip separates the two transforms.
+// Each inverse's last stage stores straight to HBM. Rows of `cols` complex
+// values are 64 or 128 bytes, so a half-warp (FP32) or quarter-warp (FP64)
+// access covers whole rows. Table values of the filter are read before the
+// wait for the tile (an L1 prefetch, no registers held).
+template <typename R, int E>
+__global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
+    k_axis(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
   using C = Cx<R>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
-  const int N = a.n, P = N / E, B = a.cols;
+  const int N = a.n, P = N / E, B = a.cols, half = N >> 1;
   const int tile_elems = N * B;
   const int stride_elems = ((tile_elems * (int)sizeof(C) + 127) & ~127) / (int)sizeof(C);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
   const int tid = threadIdx.x;
-  const int c = tid & (B - 1), p = tid / B;
   const int64_t ntiles = (int64_t)N * a.inner_chunks;
   const uint32_t tile_bytes = (uint32_t)(tile_elems * sizeof(C));
   const C *tw = reinterpret_cast<const C *>(a.tw);
-  if (tid == 0) {
+  const R *table = reinterpret_cast<const R *>(a.table);
+  const bool use_tma = a.rows_box > 0;
+  const FftStages &sf = a.st_fwd;
+  const FftStages &si = a.st_inv;
+  const int S = sf.nstages;
+  const int r0 = a.inv ? si.radix[0] : sf.radix[S - 1];
+  if (use_tma && tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int64_t t, int s) {
+  auto issue = [&](int64_t t, int sb) {
     const int64_t outer = t / a.inner_chunks;
     const int chunk = (int)(t - outer * a.inner_chunks);
-    C *dst = bufs + s * stride_elems;
-    mbar_arrive_expect_tx(&bars[s], tile_bytes);
+    C *dst = bufs + sb * stride_elems;
+    mbar_arrive_expect_tx(&bars[sb], tile_bytes);
     const int c0 = chunk * B * 2;  // innermost coordinate in reals
     for (int i = 0; i < N; i += a.rows_box) {
-      if (a.axis == 1) tma_load_3d(dst + i * B, &map, &bars[s], c0, i, (int)outer);
-      else tma_load_3d(dst + i * B, &map, &bars[s], c0, (int)outer, i);
+      if (a.axis == 1) tma_load_3d(dst + i * B, &map, &bars[sb], c0, i, (int)outer);
+      else tma_load_3d(dst + i * B, &map, &bars[sb], c0, (int)outer, i);
     }
   };
   int64_t t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
-  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-    const int s = it & 1;
+  if (use_tma && tid == 0 && t < ntiles) issue(t, 0);
+  bool abort = false;
+  for (int it = 0; t < ntiles && !abort; t += gridDim.x, ++it) {
+    const int sb = use_tma ? (it & 1) : 0;
     const int64_t tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) {
+    if (use_tma && tid == 0 && tn < ntiles) {
       fence_proxy_async_smem();
-      issue(tn, s ^ 1);
+      issue(tn, sb ^ 1);
     }
-    const bool ok = __syncthreads_and(mbar_wait(&bars[s], (uint32_t)((it >> 1) & 1), a.err));
-    if (!ok) {
-      if (tid == 0 && tn < ntiles) mbar_wait(&bars[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
-      return;
-    }
-    C *buf = bufs + s * stride_elems;
+    // thread coordinates, opaque to the optimiser so that the addresses of
+    // every stage variant are not hoisted out of the tile loop (they would
+    // stay live for the whole kernel)
+    int c = tid & (B - 1), p = tid / B;
+    asm volatile("" : "+r"(c), "+r"(p));
     const int64_t outer = t / a.inner_chunks;
     const int chunk = (int)(t - outer * a.inner_chunks);
     const int kz = chunk * B + c;
-    C *dst = reinterpret_cast<C *>(a.dst) + outer * a.outer_stride + kz;
-    const int S = a.st.nstages;
-    auto ld_first = [&](int n) {
-      C v = buf[n * B + c];
-      if (a.filter == kFiltPsi) v = apply_filter<R>(a, v, n, outer, kz);
-      return v;
-    };
+    C *buf = bufs + sb * stride_elems;
+    const int64_t gbase = outer * a.outer_stride + kz;
+    const int m_outer = a.axis == 0 ? freq_of((int)outer, N) : 0;
+    const bool nyq_outer = a.axis == 0 && (int)outer == half;
     auto ld_smem = [&](int n) { return buf[n * B + c]; };
     auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
-    auto st_glob = [&](int n, C v) {
-      if (a.filter == kFiltDelta) v = apply_filter<R>(a, v, n, outer, kz);
-      dst[(int64_t)n * a.stride] = v;
+    // V: this thread's elements at the hand-off positions p + P*b + r*N/r0
+    C V[E];
+    auto tab_index = [&](int n) {
+      const int m = freq_of(n, N);
+      return (n == half || nyq_outer) ? -1 : m * m + m_outer * m_outer + kz * kz;
     };
-    if (S == 1) {
-      stage_dispatch<R, E, INV, false>(a.st, 0, p, P, tw, ld_first, st_glob);
+    if (a.pre) {
+      with_radix<E>(r0, [&](auto rc) {
+        constexpr int RH = decltype(rc)::value;
+        const int span = N / RH;
+#pragma unroll
+        for (int b = 0; b < E / RH; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) {
+            const int q = tab_index(p + P * b + r * span);
+            if (q >= 0) prefetch_l1(table + q);
+          }
+      });
+    }
+    if (use_tma) {
+      const bool ok = __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err));
+      if (!ok) {
+        if (tid == 0 && tn < ntiles)
+          mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+        abort = true;
+        break;
+      }
     } else {
-      stage_dispatch<R, E, INV, true>(a.st, 0, p, P, tw, ld_first, st_smem);
-      for (int si = 1; si < S - 1; ++si)
-        stage_dispatch<R, E, INV, true>(a.st, si, p, P, tw, ld_smem, st_smem);
-      stage_dispatch<R, E, INV, false>(a.st, S - 1, p, P, tw, ld_smem, st_glob);
+      const C *src = reinterpret_cast<const C *>(a.src) + outer * a.outer_stride + chunk * B;
+      for (int q = tid; q < tile_elems; q += blockDim.x) {
+        const int n = q / B;
+        buf[q] = src[(int64_t)n * a.stride + (q - n * B)];
+      }
+      __syncthreads();
+    }
+    if (a.fwd)
+      for (int s2 = 0; s2 < S - 1; ++s2)
+        stage_dispatch<R, E, false, true>(sf, s2, p, P, tw, ld_smem, st_smem);
+    with_radix<E>(r0, [&](auto rc) {
+      constexpr int RH = decltype(rc)::value;
+      const int span = N / RH;
+#pragma unroll
+      for (int b = 0; b < E / RH; ++b)
+#pragma unroll
+        for (int r = 0; r < RH; ++r) V[b * RH + r] = buf[(p + P * b + r * span) * B + c];
+      if (a.fwd) {
+        StageTw<R, E, RH> tt;
+        load_twiddles<R, E, RH>(tt, p, P, sf.ns[S - 1], sf.ns_shift[S - 1], sf.tstep[S - 1], tw);
+        stage_compute<R, E, RH, false>(V, p, P, sf.ns[S - 1], sf.ns_shift[S - 1], sf.tstep[S - 1],
+                                       tt, tw);
+      }
+      if (a.pre) {
+#pragma unroll
+        for (int b = 0; b < E / RH; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) {
+            const int q = tab_index(p + P * b + r * span);
+            const R f = q >= 0 ? __ldg(table + q) : (R)0;
+            V[b * RH + r] = Cx<R>{f * V[b * RH + r].x, f * V[b * RH + r].y};
+          }
+      }
+      if (!a.inv) {  // forward only: the spectrum to dst[0]
+        C *d = reinterpret_cast<C *>(a.dst[0]) + gbase;
+#pragma unroll
+        for (int b = 0; b < E / RH; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r)
+            d[(int64_t)(p + P * b + r * span) * a.stride] = V[b * RH + r];
+      }
+    });
+    __syncthreads();  // the tile is in registers: buf becomes the inverse work buffer
+    if (!a.inv) continue;
+    for (int o = 0; o < a.nout; ++o) {
+      asm volatile("" : "+r"(c), "+r"(p));
+      C *d = reinterpret_cast<C *>(a.dst[o]) + gbase;
+      auto st_glob = [&](int n, C v) { d[(int64_t)n * a.stride] = v; };
+      if (o > 0) __syncthreads();  // the previous output's last stage has read buf
+      with_radix<E>(r0, [&](auto rc) {
+        constexpr int RH = decltype(rc)::value;
+        const int span = N / RH;
+        C W[E];
+#pragma unroll
+        for (int b = 0; b < E / RH; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) {
+            const int n = p + P * b + r * span;
+            W[b * RH + r] = apply_mul<R>(a.mul[o], V[b * RH + r], n, N);
+          }
+        StageTw<R, E, RH> none;
+        stage_compute<R, E, RH, true>(W, p, P, 1, 0, 0, none, tw);  // first inverse stage: ns = 1
+#pragma unroll
+        for (int b = 0; b < E / RH; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) {
+            const int q = (p + P * b) * RH + r;
+            if (S == 1) st_glob(q, W[b * RH + r]);
+            else buf[q * B + c] = W[b * RH + r];
+          }
+      });
+      if (S == 1) continue;
+      __syncthreads();
+      for (int s2 = 1; s2 < S - 1; ++s2)
+        stage_dispatch<R, E, true, true>(si, s2, p, P, tw, ld_smem, st_smem);
+      stage_dispatch<R, E, true, false>(si, S - 1, p, P, tw, ld_smem, st_glob);
     }
     __syncthreads();
   }
@@ -258,7 +312,7 @@ __device__ __forceinline__ R wrap_box(R x, R box) {
 template <typename R, int E>
 __global__ void k_zinv(const ZInvArgs a) {
   using C = Cx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   const int M = a.st.len, P = M / E;
   const LineLayout lay{line_ld(M)};
@@ -268,7 +322,12 @@ __global__ void k_zinv(const ZInvArgs a) {
   if (live) {
     const C *src = reinterpret_cast<const C *>(a.src) + line * M;
 #pragma unroll
-    for (int i = 0; i < E; ++i) buf[lay(l, p + P * i)] = src[p + P * i];
+    for (int i = 0; i < E; ++i) {
+      const int k = p + P * i;
+      C v = src[k];
+      if (a.mul_kz) v = C{-(R)k * v.y, (R)k * v.x};  // i m_z, m_z = k for k < N/2
+      buf[lay(l, k)] = v;
+    }
   }
   __syncthreads();
   C z[E];
@@ -380,7 +439,7 @@ static EncodeTiledFn encode_tiled_fn() {
 // 2 * N/2 reals), with a box of `cols` complex columns by rows_box points
 // along the pass axis.
 template <typename R>
-static cudaError_t make_map(CUtensorMap *m, const ColArgs &a) {
+static cudaError_t make_map(CUtensorMap *m, const AxisArgs &a) {
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t half = (cuuint64_t)(a.n / 2);
@@ -399,8 +458,6 @@ static cudaError_t make_map(CUtensorMap *m, const ColArgs &a) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t colt_smem_bytes(int len, int cols, size_t complex_bytes);
-
 template <typename K>
 static int persistent_blocks(K kernel, int threads, size_t smem, int64_t tiles) {
   int dev = 0, sms = 0, per = 0;
@@ -414,45 +471,19 @@ static int persistent_blocks(K kernel, int threads, size_t smem, int64_t tiles) 
 }
 
 template <typename R>
-cudaError_t launch_col(const ColArgs &a, bool inverse, cudaStream_t s) {
-  const int64_t outer = a.n;  // N outer indices in both passes
-  if (a.rows_box > 0) {
-    CUtensorMap map;
-    cudaError_t e = make_map<R>(&map, a);
-    if (e != cudaSuccess) return e;
-    const int P = a.n / a.e;
-    const unsigned threads = (unsigned)(P * a.cols);
-    const size_t smem = colt_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
-    const int64_t tiles = outer * a.inner_chunks;
-    GG_DISPATCH_E(a.e, {
-      if (inverse) {
-        auto kern = k_colt<R, EE, true>;
-        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-        kern<<<persistent_blocks(kern, threads, smem, tiles), threads, smem, s>>>(map, a);
-      } else {
-        auto kern = k_colt<R, EE, false>;
-        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-        kern<<<persistent_blocks(kern, threads, smem, tiles), threads, smem, s>>>(map, a);
-      }
-    });
-    return cudaGetLastError();
-  }
-  const int P = a.n / a.st.e;
-  const size_t smem = col_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
-  const unsigned blocks = (unsigned)(outer * a.inner_chunks);
+cudaError_t launch_axis(const AxisArgs &a, cudaStream_t s) {
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  cudaError_t e;
+  if (a.rows_box > 0 && (e = make_map<R>(&map, a)) != cudaSuccess) return e;
+  const int P = a.n / a.e;
   const unsigned threads = (unsigned)(P * a.cols);
-  GG_DISPATCH_E(a.st.e, {
-    if (inverse) {
-      auto kern = k_col<R, EE, true>;
-      cudaError_t e = set_smem(kern, smem);
-      if (e != cudaSuccess) return e;
-      kern<<<blocks, threads, smem, s>>>(a);
-    } else {
-      auto kern = k_col<R, EE, false>;
-      cudaError_t e = set_smem(kern, smem);
-      if (e != cudaSuccess) return e;
-      kern<<<blocks, threads, smem, s>>>(a);
-    }
+  const size_t smem = axis_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
+  const int64_t tiles = (int64_t)a.n * a.inner_chunks;
+  GG_DISPATCH_E(a.e, {
+    auto kern = k_axis<R, EE>;
+    if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+    kern<<<persistent_blocks(kern, threads, smem, tiles), threads, smem, s>>>(map, a);
   });
   return cudaGetLastError();
 }
@@ -473,25 +504,30 @@ cudaError_t launch_zinv(const ZInvArgs &a, cudaStream_t s) {
 }
 
 // Largest block each kernel can launch with (registers bound it), so the host
-// can size tiles: kind 0 = forward z, 1 = strided, 2 = inverse z.
+// can size tiles: kind 0 = forward z, 2 = inverse z, 3 = strided.
 template <typename R>
 int max_block_threads(int kind, int e) {
   cudaFuncAttributes fa{};
   cudaError_t err = cudaErrorInvalidValue;
   GG_DISPATCH_E(e, {
+#ifdef GG_AXIS_TU
+    if (kind == 3) err = cudaFuncGetAttributes(&fa, k_axis<R, EE>);
+#else
     if (kind == 0) err = cudaFuncGetAttributes(&fa, k_zfwd<R, EE>);
-    else if (kind == 1) err = cudaFuncGetAttributes(&fa, k_col<R, EE, false>);
-    else if (kind == 3) err = cudaFuncGetAttributes(&fa, k_colt<R, EE, false>);
-    else err = cudaFuncGetAttributes(&fa, k_zinv<R, EE>);
+    else if (kind == 2) err = cudaFuncGetAttributes(&fa, k_zinv<R, EE>);
+#endif
   });
   return err == cudaSuccess ? fa.maxThreadsPerBlock : -1;
 }
 
-#define GG_INSTANTIATE(R)                                                         \
+#define GG_INSTANTIATE_Z(R)                                                       \
   template cudaError_t launch_noise<R>(const NoiseArgs &, cudaStream_t);          \
   template cudaError_t launch_zfwd<R>(const ZFwdArgs &, cudaStream_t);            \
-  template cudaError_t launch_col<R>(const ColArgs &, bool, cudaStream_t);        \
-  template cudaError_t launch_zinv<R>(const ZInvArgs &, cudaStream_t);          \
-  template int max_block_threads<R>(int, int);
+  template cudaError_t launch_zinv<R>(const ZInvArgs &, cudaStream_t);            \
+  template <> int max_block_threads_z<R>(int kind, int e) { return max_block_threads<R>(kind, e); }
+
+#define GG_INSTANTIATE_AXIS(R)                                                    \
+  template cudaError_t launch_axis<R>(const AxisArgs &, cudaStream_t);            \
+  template <> int max_block_threads_axis<R>(int e) { return max_block_threads<R>(3, e); }
 
 }  // namespace gg

@@ -24,13 +24,9 @@ size_t zpass_smem_bytes(int half_len, int lines, size_t complex_bytes) {
   return (size_t)line_ld(half_len) * (size_t)lines * complex_bytes;
 }
 
-size_t colt_smem_bytes(int len, int cols, size_t complex_bytes) {
+size_t axis_smem_bytes(int len, int cols, size_t complex_bytes) {
   const size_t tile = ((size_t)len * cols * complex_bytes + 127) & ~(size_t)127;
   return 128 + 2 * tile;
-}
-
-size_t col_smem_bytes(int len, int cols, size_t complex_bytes) {
-  return (size_t)col_words(len, cols) * complex_bytes;
 }
 
 }  // namespace gg

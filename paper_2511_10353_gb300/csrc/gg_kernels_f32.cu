@@ -1,7 +1,6 @@
-// FP32 instantiation of the path's kernels (FFT and filter arithmetic in FP32,
-// tables and twiddles generated in FP64 on the host and rounded once).
+// FP32 (FFT arithmetic in FP32; tables and twiddles generated in FP64 and rounded once) instantiation of the z passes and the noise kernel.
 #include "gg_kernels.cuh"
 
 namespace gg {
-GG_INSTANTIATE(float)
+GG_INSTANTIATE_Z(float)
 }  // namespace gg

@@ -1,6 +1,6 @@
-// FP64 instantiation of the path's kernels (the plain double-precision path).
+// FP64 (the plain double-precision path) instantiation of the z passes and the noise kernel.
 #include "gg_kernels.cuh"
 
 namespace gg {
-GG_INSTANTIATE(double)
+GG_INSTANTIATE_Z(double)
 }  // namespace gg
