@@ -1,0 +1,115 @@
+"""The 1536^3 precision workload: FP32 path at full size, in the bench's launch shape.
+
+1536^3, L = 2000 Mpc/h, Eisenstein-Hu no-wiggle (Om=.31, h=.68, ns=.965,
+s8=.81), z = 100. The complete FP64 oracle does not fit this host's memory at
+this size, so:
+* the Philox words and W values of sampled cells are compared with the oracle
+  one by one (bit-exact words);
+* a planted Fourier mode W = cos(k0.x) must give psi = -s k0/|k0|^2 sin(k0.x)
+  with s from the oracle's P(k0) and growth, checked on sampled cells;
+* each displacement component of the FP32 path is within 1e-5 relative L2
+  of the GPU FP64 path (which the other tests pin to the oracle at <= 1e-12).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import noise as onoise
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EH_NW = dict(omega_m=0.31, h=0.68, n_s=0.965, sigma_8=0.81, tf="eh_nw", omega_l=-1.0,
+             omega_b=0.049, t_cmb=2.7255)
+N, BOX, Z = 1536, 2000.0, 100.0
+
+
+@pytest.fixture(scope="module")
+def gg():
+    from paper_2511_10353_gb300 import build
+    build.build(verbose=False)
+    import paper_2511_10353_gb300 as m
+    if torch.cuda.get_device_properties(0).total_memory < 200e9:
+        pytest.skip("needs a GPU with >= 200 GB")
+    return m
+
+
+def _sample_idx(count, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(N ** 3, size=count, replace=False)).astype(np.int64)
+
+
+def test_noise_words_and_values_sampled(gg):
+    idx = _sample_idx(200000)
+    groups = np.unique(idx >> 2)
+    words = gg.noise_bits(1, 0, int(groups.max()) + 1)  # all groups up to the largest sampled
+    got = words.cpu().numpy().view(np.uint32)[groups]
+    assert np.array_equal(got, onoise.noise_bits(1, groups.astype(np.uint64)))
+    del words
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f32")
+    w = plan.white_noise(seed=1).reshape(-1)
+    vals = w[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    want = onoise.noise_at(1, idx)
+    assert np.sqrt(np.mean((vals - want) ** 2)) < 1e-6 and np.abs(vals - want).max() < 1e-3
+    del w
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def test_planted_mode_sampled(gg):
+    from tests.oracle_cases import cosmology_from
+    c = cosmology_from(EH_NW)
+    m0 = (3, -7, 11)
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f32")
+    i = torch.arange(N, device="cuda", dtype=torch.float64)
+    ph = (2 * math.pi / N) * (m0[0] * i[:, None, None] + m0[1] * i[None, :, None])
+    noise = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    for ix in range(0, N, 64):  # cos(k0.x) written in slabs to bound the temporaries
+        noise[ix:ix + 64] = torch.cos(ph[ix:ix + 64] + (2 * math.pi / N) * m0[2] * i[None, None, :]).float()
+    del ph
+    psi = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    idx = _sample_idx(100000, 1)
+    ix, iy, iz = idx // (N * N), (idx // N) % N, idx % N
+    phase = 2 * math.pi * (m0[0] * ix + m0[1] * iy + m0[2] * iz) / N
+    k0 = 2 * math.pi / BOX * np.array(m0, dtype=float)
+    kk = math.sqrt((k0 ** 2).sum())
+    s = plan.info["growth"] * math.sqrt(c.power(kk) * N ** 3 / BOX ** 3)
+    for j in range(3):
+        out = {"psi": [psi if a == j else None for a in range(3)], "pos": [None] * 3, "vel": [None] * 3}
+        plan.zeldovich(noise=noise, out=out)
+        plan.sync()
+        got = psi.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+        want = -s * k0[j] / kk ** 2 * np.sin(phase)
+        scale = s * abs(k0[j]) / kk ** 2
+        assert np.abs(got - want).max() < 2e-5 * scale, j
+    del noise, psi
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def test_fp32_within_1e5_of_fp64(gg):
+    errs = []
+    for j in range(3):
+        p32 = gg.Plan(N, BOX, EH_NW, Z, "f32")
+        a = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        p32.zeldovich(seed=1, out={"psi": [a if c == j else None for c in range(3)],
+                                   "pos": [None] * 3, "vel": [None] * 3})
+        p32.sync()
+        p32.close()
+        torch.cuda.empty_cache()
+        p64 = gg.Plan(N, BOX, EH_NW, Z, "f64")
+        b = torch.empty((N, N, N), dtype=torch.float64, device="cuda")
+        p64.zeldovich(seed=1, out={"psi": [b if c == j else None for c in range(3)],
+                                   "pos": [None] * 3, "vel": [None] * 3})
+        p64.sync()
+        p64.close()
+        num = den = 0.0
+        for ix in range(0, N, 128):
+            d = a[ix:ix + 128].double() - b[ix:ix + 128]
+            num += float((d * d).sum())
+            den += float((b[ix:ix + 128] ** 2).sum())
+        errs.append(math.sqrt(num / den))
+        del a, b
+        torch.cuda.empty_cache()
+    assert max(errs) < 1e-5, errs
