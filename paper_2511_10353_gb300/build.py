@@ -22,6 +22,8 @@ LIB = os.path.join(HERE, "libgg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = [
+    "gg_ct_f32.cu",
+    "gg_ct_f64.cu",
     "gg_axis_f32.cu",
     "gg_axis_f64.cu",
     "gg_kernels_f32.cu",

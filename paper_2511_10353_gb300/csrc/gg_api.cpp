@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <utility>
 #include <new>
 #include <string>
 #include <vector>
@@ -323,14 +324,32 @@ gg::AxisArgs axis_args(gg_plan_t *plan, int axis, const void *src) {
   return c;
 }
 
+// One strided pass; the size-specialised kernel where N has one. When that
+// kernel keeps one output per launch, a two-output pass becomes two launches
+// reading the same input, the in-place output (dst == src) last.
 template <typename R>
 gg_status launch_axis_timed(gg_plan_t *plan, const gg::AxisArgs &c, int kind, const char *what) {
   const double cb = (double)plan->cells * sizeof(R);
+  const bool spec = gg::spec_has<R>(c.n);
+  const int max_out = spec ? gg::spec_axis_max_out<R>(c.n) : 3;
+  if (c.inv && c.nout > max_out) {
+    int order[3] = {0, 1, 2};
+    if (c.nout == 2 && c.dst[0] == c.src) std::swap(order[0], order[1]);
+    for (int i = 0; i < c.nout; ++i) {
+      gg::AxisArgs one = c;
+      one.nout = 1;
+      one.dst[0] = c.dst[order[i]];
+      one.mul[0] = c.mul[order[i]];
+      gg_status st = launch_axis_timed<R>(plan, one, kind, what);
+      if (st != GG_OK) return st;
+    }
+    return GG_OK;
+  }
   const double bytes = (c.fwd && !c.inv ? 2 : 1 + c.nout) * cb;
   cudaError_t e;
   {
     ProfScope ps(plan, kind, bytes);
-    e = gg::launch_axis<R>(c, plan->stream);
+    e = spec ? gg::spec_axis<R>(c, plan->stream) : gg::launch_axis<R>(c, plan->stream);
   }
   return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, what);
 }
@@ -353,7 +372,7 @@ gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
   cudaError_t e;
   {
     ProfScope ps(plan, kZFwd, noise ? 2 * cb : cb);
-    e = gg::launch_zfwd<R>(z, plan->stream);
+    e = gg::spec_has<R>(n) ? gg::spec_zfwd<R>(z, plan->stream) : gg::launch_zfwd<R>(z, plan->stream);
   }
   if (e != cudaSuccess) return cuda_fail(plan, e, "z forward pass");
   gg::AxisArgs c = axis_args<R>(plan, 1, plan->work);
@@ -386,12 +405,13 @@ gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void 
   z.st = plan->st_half;
   z.tw_half = plan->tab.tw_half;
   z.tw_full = plan->tab.tw_n;
+  z.err = plan->err;
   const double cb = (double)plan->cells * sizeof(R);
   const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
   cudaError_t e;
   {
     ProfScope ps(plan, kZInv, (1 + outs) * cb);
-    e = gg::launch_zinv<R>(z, plan->stream);
+    e = gg::spec_has<R>(n) ? gg::spec_zinv<R>(z, plan->stream) : gg::launch_zinv<R>(z, plan->stream);
   }
   return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, "z inverse pass");
 }

@@ -1,0 +1,218 @@
+// Compile-time FFT codelets for the grid sizes of the named workloads.
+//
+// The run-time kernels in gg_kernels.cuh take N, the radix schedule and the
+// tile width as parameters; every shared-memory access then needs its own
+// index arithmetic. Here N, the tile width and the schedule are template
+// constants: stage radices, spans, twiddle steps and butterfly positions fold
+// into immediate offsets, and the stage loop unrolls. The data flow is the
+// same as the run-time kernels' (same passes, same tiles, same rounding of
+// the FP64-generated tables).
+#pragma once
+
+#include <cuda.h>
+
+#include "gg_device.cuh"
+
+namespace gg {
+namespace ct {
+
+// ------------------------------------------------------------ schedules
+struct Fac {
+  int a, b;  // n = 2^a 3^b
+};
+__host__ __device__ constexpr Fac factor(int n) {
+  Fac f{0, 0};
+  while (n % 2 == 0) { n /= 2; ++f.a; }
+  while (n % 3 == 0) { n /= 3; ++f.b; }
+  return f;
+}
+__host__ __device__ constexpr int nstages(int n) {
+  const Fac f = factor(n);
+  return f.a / 3 + (f.a % 3 ? 1 : 0) + f.b;
+}
+// forward schedule: radix 8 first, then 4 or 2, then the 3s
+__host__ __device__ constexpr int radix_fwd(int n, int s) {
+  const Fac f = factor(n);
+  const int n8 = f.a / 3;
+  if (s < n8) return 8;
+  s -= n8;
+  if (f.a % 3) {
+    if (s == 0) return f.a % 3 == 2 ? 4 : 2;
+    s -= 1;
+  }
+  return 3;
+}
+// the inverse transforms use the same radices in reverse order, so that the
+// first inverse stage has the radix of the last forward stage
+__host__ __device__ constexpr int radix_of(int n, int s, bool inv) {
+  return inv ? radix_fwd(n, nstages(n) - 1 - s) : radix_fwd(n, s);
+}
+__host__ __device__ constexpr int ns_of(int n, int s, bool inv) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= radix_of(n, i, inv);
+  return p;
+}
+// elements per thread: the least common multiple of the radices
+__host__ __device__ constexpr int elems(int n) {
+  const Fac f = factor(n);
+  const int p2 = f.a >= 3 ? 8 : (f.a == 2 ? 4 : (f.a == 1 ? 2 : 1));
+  return p2 * (f.b ? 3 : 1);
+}
+
+// k = j mod NS for j = p + P*b, 0 <= p < P, 0 <= b < NB, folded at compile time
+template <int NS, int P, int NB>
+__device__ __forceinline__ int k_of(int p, int b) {
+  if constexpr (NS == 1) {
+    return 0;
+  } else if constexpr (P % NS == 0) {
+    return p % NS;
+  } else if constexpr (P * NB <= NS) {
+    return p + P * b;  // j < NS
+  } else {
+    return (p + P * b) % NS;
+  }
+}
+
+// One Stockham stage of a length-N transform, stage index SI of the forward
+// (INV = false) or inverse schedule, for the butterflies j = p + P*b of this
+// thread. ld(n) reads element n of the stage input, st(n, v) writes element n
+// of its output; with SYNC the stage runs in place in shared memory.
+template <typename R, int N, int SI, bool INV, bool SYNC, class Ld, class St>
+__device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
+                                      const St &st) {
+  constexpr int E = elems(N);
+  constexpr int RAD = radix_of(N, SI, INV);
+  constexpr int NS = ns_of(N, SI, INV);
+  constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
+  asm volatile("" : "+r"(p));
+  Cx<R> w1[NB];
+  if constexpr (NS > 1 && sizeof(R) == 4) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) w1[b] = ldg_c(tw + k_of<NS, P, NB>(p, b) * TSTEP);
+  }
+  Cx<R> v[E];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b * RAD + r] = ld(p + P * b + r * SPAN);
+  if (SYNC) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if constexpr (NS > 1) {
+      if constexpr (sizeof(R) == 4) {
+        twiddle_powers<RAD, INV>(&v[b * RAD], w1[b]);
+      } else {
+        const int k = k_of<NS, P, NB>(p, b);
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          const Cx<R> w = ldg_c(tw + k * TSTEP * r);
+          v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
+        }
+      }
+    }
+    Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int k = k_of<NS, P, NB>(p, b);
+    const int base = (p + P * b - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) st(base + r * NS, v[b * RAD + r]);
+  }
+  if (SYNC) __syncthreads();
+}
+
+// Stages FIRST .. LAST-1 in place in shared memory.
+template <typename R, int N, bool INV, int FIRST, int LAST, class Ld, class St>
+__device__ __forceinline__ void stages(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
+                                       const St &st) {
+  if constexpr (FIRST < LAST) {
+    stage<R, N, FIRST, INV, true>(p, tw, ld, st);
+    stages<R, N, INV, FIRST + 1, LAST>(p, tw, ld, st);
+  }
+}
+
+// The last stage of a schedule, outputs kept in registers: on return v holds
+// element j + r*N/RAD at v[b*RAD + r] (j = p + P*b).
+template <typename R, int N, bool INV, class Ld>
+__device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
+                                                Cx<R> *v) {
+  constexpr int S = nstages(N);
+  constexpr int E = elems(N);
+  constexpr int RAD = radix_of(N, S - 1, INV);
+  constexpr int NS = ns_of(N, S - 1, INV);
+  constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
+  static_assert(NS * RAD == N, "last stage");
+  asm volatile("" : "+r"(p));
+  Cx<R> w1[NB];
+  if constexpr (NS > 1 && sizeof(R) == 4) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) w1[b] = ldg_c(tw + k_of<NS, P, NB>(p, b) * TSTEP);
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b * RAD + r] = ld(p + P * b + r * SPAN);
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if constexpr (NS > 1) {
+      if constexpr (sizeof(R) == 4) {
+        twiddle_powers<RAD, INV>(&v[b * RAD], w1[b]);
+      } else {
+        const int k = k_of<NS, P, NB>(p, b);
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          const Cx<R> w = ldg_c(tw + k * TSTEP * r);
+          v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
+        }
+      }
+    }
+    Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
+  }
+}
+
+// ------------------------------------------------------------ tile policy
+// Strided passes: columns per tile (rows of 128 bytes where two tiles fit in
+// shared memory and the CTA stays within 512 threads) and whether the spectrum
+// of two outputs may stay in registers (E <= 16 complex values per thread
+// under 128 registers; larger E runs one output per launch).
+template <typename R, int N> struct AxisPolicy {
+  static constexpr int E = elems(N);
+  static constexpr int P = N / E;
+  static constexpr int CB = 2 * (int)sizeof(R);
+  static constexpr int pick() {
+    int b = 128 / CB;
+    while (b > 1 && ((N / 2) % b != 0 || P * b > 512 || 2 * (N * b * CB) > 200 * 1024)) b /= 2;
+    return b;
+  }
+  static constexpr int B = pick();
+  static constexpr int THREADS = P * B;
+  // two outputs keep the handed-off spectrum (2E words per complex word size)
+  // live beside a stage's own E values: estimate against the register budget
+  static constexpr int REG_BUDGET = 65536 / THREADS < 255 ? 65536 / THREADS : 255;
+  static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
+  static constexpr int MAX_OUT = REG_NEED <= REG_BUDGET ? 2 : 1;
+  static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
+};
+
+// z passes: lines per tile (~256 threads, two dense tiles + one padded tile
+// within 160 KB).
+template <typename R, int N> struct ZPolicy {
+  static constexpr int M = N / 2;
+  static constexpr int E = elems(M);
+  static constexpr int P = M / E;
+  static constexpr int CB = 2 * (int)sizeof(R);
+  static constexpr int LD = M + (M >> 4) + 1;
+  static constexpr int pick() {
+    int l = 1;
+    while (l < 64 && P * l * 2 <= 256 && (2 * (2 * l) * M + 2 * l * LD) * CB <= 160 * 1024) l *= 2;
+    return l;
+  }
+  static constexpr int L = pick();
+  static constexpr int THREADS = P * L;
+  static constexpr int DENSE = L * M;        // complex values of one dense tile
+  static constexpr int WORK = L * LD;        // complex values of the padded tile
+};
+
+}  // namespace ct
+}  // namespace gg

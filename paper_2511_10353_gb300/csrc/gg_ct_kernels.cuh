@@ -1,0 +1,383 @@
+// Size-specialised kernels of the three transform passes (see gg_ct.cuh).
+// Included by gg_ct_f32.cu / gg_ct_f64.cu, which instantiate them for the
+// grid sizes of the named workloads; every other size runs the run-time
+// kernels of gg_kernels.cuh.
+#pragma once
+
+#include "gg_ct.cuh"
+#include "gg_launch.cuh"
+
+namespace gg {
+
+__device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n : n - N; }
+
+// ------------------------------------------------------------ strided pass
+// The pass of k_axis (gg_kernels.cuh) with N and the tile width fixed:
+// persistent CTAs, TMA double buffering, forward stages in place in shared
+// memory, the spectrum handed to the inverse stages in registers, each
+// inverse's last stage storing straight to HBM.
+template <typename R, int N>
+__global__ void __launch_bounds__(ct::AxisPolicy<R, N>::THREADS, 1)
+    k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
+  using C = Cx<R>;
+  using Pol = ct::AxisPolicy<R, N>;
+  constexpr int B = Pol::B, E = Pol::E, P = Pol::P, HALF = N / 2, S = ct::nstages(N);
+  constexpr int TILE = N * B;
+  constexpr int TILE_STRIDE = (int)(((TILE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
+  constexpr int INNER = HALF / B;
+  constexpr int RH = ct::radix_of(N, 0, true);  // radix at the register hand-off
+  static_assert(RH == ct::radix_of(N, S - 1, false), "hand-off radix");
+  constexpr int SPAN = N / RH, NB = E / RH;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  C *bufs = reinterpret_cast<C *>(smem_raw + 128);
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (int64_t)N * INNER;
+  const C *tw = reinterpret_cast<const C *>(a.tw);
+  const R *table = reinterpret_cast<const R *>(a.table);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t t, int sb) {
+    const int64_t outer = t / INNER;
+    const int chunk = (int)(t - outer * INNER);
+    C *dst = bufs + sb * TILE_STRIDE;
+    mbar_arrive_expect_tx(&bars[sb], (uint32_t)(TILE * sizeof(C)));
+#pragma unroll
+    for (int i = 0; i < N; i += Pol::ROWS_BOX) {
+      if (a.axis == 1) tma_load_3d(dst + i * B, &map, &bars[sb], chunk * B * 2, i, (int)outer);
+      else tma_load_3d(dst + i * B, &map, &bars[sb], chunk * B * 2, (int)outer, i);
+    }
+  };
+  int64_t t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int sb = it & 1;
+    const int64_t tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {
+      fence_proxy_async_smem();
+      issue(tn, sb ^ 1);
+    }
+    int c = tid & (B - 1), p = tid / B;
+    asm volatile("" : "+r"(c), "+r"(p));
+    const int64_t outer = t / INNER;
+    const int chunk = (int)(t - outer * INNER);
+    const int kz = chunk * B + c;
+    C *buf = bufs + sb * TILE_STRIDE;
+    const int64_t gbase = outer * a.outer_stride + kz;
+    const int m_outer = a.axis == 0 ? ct_freq((int)outer, N) : 0;
+    const bool nyq_outer = a.axis == 0 && (int)outer == HALF;
+    auto tab_index = [&](int n) {
+      const int m = ct_freq(n, N);
+      return (n == HALF || nyq_outer) ? -1 : m * m + m_outer * m_outer + kz * kz;
+    };
+    if (a.pre) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+          const int q = tab_index(p + P * b + r * SPAN);
+          if (q >= 0) prefetch_l1(table + q);
+        }
+    }
+    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err));
+    if (!ok) {
+      if (tid == 0 && tn < ntiles) mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+      return;
+    }
+    auto ld_smem = [&](int n) { return buf[n * B + c]; };
+    auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
+    C V[E];
+    if (a.fwd) {
+      ct::stages<R, N, false, 0, S - 1>(p, tw, ld_smem, st_smem);
+      ct::last_stage_regs<R, N, false>(p, tw, ld_smem, V);
+    } else {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < RH; ++r) V[b * RH + r] = buf[(p + P * b + r * SPAN) * B + c];
+    }
+    if (a.pre) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+          const int q = tab_index(p + P * b + r * SPAN);
+          const R f = q >= 0 ? __ldg(table + q) : (R)0;
+          V[b * RH + r] = C{f * V[b * RH + r].x, f * V[b * RH + r].y};
+        }
+    }
+    if (!a.inv) {  // forward only: the spectrum to dst[0]
+      C *d = reinterpret_cast<C *>(a.dst[0]) + gbase;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * a.stride] = V[b * RH + r];
+      __syncthreads();
+      continue;
+    }
+    __syncthreads();  // the tile is in registers: buf becomes the inverse work buffer
+    for (int o = 0; o < a.nout; ++o) {
+      asm volatile("" : "+r"(c), "+r"(p));
+      C *d = reinterpret_cast<C *>(a.dst[o]) + gbase;
+      auto st_glob = [&](int n, C v) { d[(int64_t)n * a.stride] = v; };
+      C W[E];
+      const bool im = a.mul[o] == kMulIm;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+          const int n = p + P * b + r * SPAN;
+          const C v = V[b * RH + r];
+          const R f = n == HALF ? (R)0 : (R)ct_freq(n, N);
+          W[b * RH + r] = im ? C{-f * v.y, f * v.x} : v;
+        }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Butterfly<RH, true, C>::run(&W[b * RH]);  // inverse stage 0
+      if (o > 0) __syncthreads();  // the previous output's last stage has read buf
+      if constexpr (S == 1) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) st_glob((p + P * b) * RH + r, W[b * RH + r]);
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) buf[((p + P * b) * RH + r) * B + c] = W[b * RH + r];
+        __syncthreads();
+        ct::stages<R, N, true, 1, S - 1>(p, tw, ld_smem, st_smem);
+        ct::stage<R, N, S - 1, true, false>(p, tw, ld_smem, st_glob);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ z passes
+// Padded line layout of the z-pass work tile: element n of line l at
+// l * LD + n + n / 16 (pairs (2q, 2q+1) never straddle a pad).
+template <int LD> __device__ __forceinline__ int zpad(int l, int n) { return l * LD + n + (n >> 4); }
+
+// Inverse z pass (c2r) + Eq. 3 epilogue, persistent: one thread bulk-copies
+// the next block of L contiguous half-spectrum lines into a dense shared
+// buffer while the CTA works on the current one. The c2r pre-processing reads
+// the dense buffer and writes the padded work tile; the transform runs there;
+// the last stage's outputs (natural order) feed the epilogue from registers.
+template <typename R, int N>
+__global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zinv_ct(const ZInvArgs a) {
+  using C = Cx<R>;
+  using Pol = ct::ZPolicy<R, N>;
+  constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
+  constexpr int S = ct::nstages(M);
+  constexpr int RL = ct::radix_of(M, S - 1, true), SPANL = M / RL, NBL = E / RL;
+  constexpr int DENSE_STRIDE = (int)(((Pol::DENSE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  C *dense = reinterpret_cast<C *>(smem_raw + 128);
+  C *work = dense + 2 * DENSE_STRIDE;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = a.nlines / L;
+  const C *tw_half = reinterpret_cast<const C *>(a.tw_half);
+  const C *twf = reinterpret_cast<const C *>(a.tw_full);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t t, int sb) {
+    mbar_arrive_expect_tx(&bars[sb], (uint32_t)(Pol::DENSE * sizeof(C)));
+    bulk_load(dense + sb * DENSE_STRIDE, reinterpret_cast<const C *>(a.src) + t * Pol::DENSE,
+              (uint32_t)(Pol::DENSE * sizeof(C)), &bars[sb]);
+  };
+  const R box = (R)a.box, cell = (R)a.cell, qo = (R)a.q_offset, vfac = (R)a.vfac;
+  int64_t t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int sb = it & 1;
+    const int64_t tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {
+      fence_proxy_async_smem();
+      issue(tn, sb ^ 1);
+    }
+    int l = tid / P, p = tid - (tid / P) * P;
+    asm volatile("" : "+r"(l), "+r"(p));
+    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err));
+    if (!ok) {
+      if (tid == 0 && tn < ntiles) mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+      return;
+    }
+    const C *dl = dense + sb * DENSE_STRIDE + l * M;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int k = p + P * i;
+      C xk = dl[k];
+      C xm = k ? dl[M - k] : C{(R)0, (R)0};
+      if (a.mul_kz) {  // i m_z on both members of the pair
+        xk = C{-(R)k * xk.y, (R)k * xk.x};
+        xm = C{-(R)(M - k) * xm.y, (R)(M - k) * xm.x};
+      }
+      const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
+      const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
+      work[zpad<LD>(l, k)] = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
+    }
+    __syncthreads();
+    auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
+    auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
+    ct::stages<R, M, true, 0, S - 1>(p, tw_half, ld_w, st_w);
+    C v[E];
+    ct::last_stage_regs<R, M, true>(p, tw_half, ld_w, v);
+    const int64_t line = t * L + l;
+    const int64_t ix = line / a.n, iy = line - ix * a.n;
+    const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
+    C *psi = a.psi ? reinterpret_cast<C *>(a.psi) + line * M : nullptr;
+    C *pos = a.pos ? reinterpret_cast<C *>(a.pos) + line * M : nullptr;
+    C *vel = a.vel ? reinterpret_cast<C *>(a.vel) + line * M : nullptr;
+#pragma unroll
+    for (int b = 0; b < NBL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int n = p + P * b + r * SPANL;
+        const C z = v[b * RL + r];
+        if (psi) psi[n] = z;
+        if (pos) {
+          R q0 = qline, q1 = qline;
+          if (a.comp == 2) {
+            q0 = ((R)(2 * n) + qo) * cell;
+            q1 = ((R)(2 * n + 1) + qo) * cell;
+          }
+          pos[n] = C{wrap_box<R>(q0 + z.x, box), wrap_box<R>(q1 + z.y, box)};
+        }
+        if (vel) vel[n] = C{vfac * z.x, vfac * z.y};
+      }
+    __syncthreads();
+  }
+}
+
+// Forward z pass: Philox noise (or caller noise) of L lines into the padded
+// work tile, the length-N/2 transform in place, then the real-input unpacking
+// X_k = (Z_k + conj Z_{M-k})/2 - i/2 e^{-2 pi i k/N} (Z_k - conj Z_{M-k}).
+template <typename R, int N>
+__global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zfwd_ct(const ZFwdArgs a) {
+  using C = Cx<R>;
+  using Pol = ct::ZPolicy<R, N>;
+  constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
+  constexpr int S = ct::nstages(M);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C *work = reinterpret_cast<C *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int64_t ntiles = a.nlines / L;
+  const C *tw_half = reinterpret_cast<const C *>(a.tw_half);
+  const C *twf = reinterpret_cast<const C *>(a.tw_full);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int l = tid / P, p = tid - (tid / P) * P;
+    asm volatile("" : "+r"(l), "+r"(p));
+    const int64_t line = t * L + l;
+    if (a.noise) {
+      const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
+#pragma unroll
+      for (int i = 0; i < E; ++i) work[zpad<LD>(l, p + P * i)] = src[p + P * i];
+    } else {
+      static_assert(N % 4 == 0, "lines start on a Philox group");
+      const uint64_t g0 = (uint64_t)line * (uint64_t)(N / 4);
+#pragma unroll
+      for (int i = 0; i < E / 2; ++i) {
+        const int q = p + P * i;
+        R w[4];
+        gauss4(noise_words(a.seed, g0 + q), w);
+        work[zpad<LD>(l, 2 * q)] = C{w[0], w[1]};
+        work[zpad<LD>(l, 2 * q + 1)] = C{w[2], w[3]};
+      }
+    }
+    __syncthreads();
+    auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
+    auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
+    ct::stages<R, M, false, 0, S>(p, tw_half, ld_w, st_w);
+    C *dst = reinterpret_cast<C *>(a.out) + line * M;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int k = p + P * i;
+      const C zk = work[zpad<LD>(l, k)];
+      const C zm = work[zpad<LD>(l, k ? M - k : 0)];
+      const C fe = {(R)0.5 * (zk.x + zm.x), (R)0.5 * (zk.y - zm.y)};
+      const C fo = {(R)0.5 * (zk.y + zm.y), (R)-0.5 * (zk.x - zm.x)};
+      dst[k] = cadd(fe, cmul(fo, ldg_c(twf + k)));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ launchers
+template <typename R, int N>
+cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
+  using Pol = ct::AxisPolicy<R, N>;
+  AxisArgs a = in;
+  a.cols = Pol::B;
+  a.inner_chunks = (N / 2) / Pol::B;
+  a.rows_box = Pol::ROWS_BOX;
+  a.e = Pol::E;
+  CUtensorMap map;
+  cudaError_t e = make_map<R>(&map, a);
+  if (e != cudaSuccess) return e;
+  const size_t tile = ((size_t)N * Pol::B * 2 * sizeof(R) + 127) & ~(size_t)127;
+  const size_t smem = 128 + 2 * tile;
+  auto kern = k_axis_ct<R, N>;
+  if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+  kern<<<persistent_blocks(kern, Pol::THREADS, smem, (int64_t)N * a.inner_chunks), Pol::THREADS,
+         smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
+  using Pol = ct::ZPolicy<R, N>;
+  const size_t dense = (Pol::DENSE * 2 * sizeof(R) + 127) & ~(size_t)127;
+  const size_t smem = 128 + 2 * dense + (size_t)Pol::WORK * 2 * sizeof(R);
+  auto kern = k_zinv_ct<R, N>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<persistent_blocks(kern, Pol::THREADS, smem, a.nlines / Pol::L), Pol::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+cudaError_t ct_launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
+  using Pol = ct::ZPolicy<R, N>;
+  const size_t smem = (size_t)Pol::WORK * 2 * sizeof(R);
+  auto kern = k_zfwd_ct<R, N>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<persistent_blocks(kern, Pol::THREADS, smem, a.nlines / Pol::L), Pol::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Run-time dispatch over the specialised sizes. NS is a list of N values.
+template <typename R, int... NS> struct CtTable {
+  static bool has(int n) { return ((n == NS) || ...); }
+  static int axis_max_out(int n) {
+    int m = 0;
+    ((m = (n == NS) ? ct::AxisPolicy<R, NS>::MAX_OUT : m), ...);
+    return m;
+  }
+  static cudaError_t axis(const AxisArgs &a, cudaStream_t s) {
+    cudaError_t e = cudaErrorInvalidValue;
+    ((a.n == NS ? (e = ct_launch_axis<R, NS>(a, s), 0) : 0), ...);
+    return e;
+  }
+  static cudaError_t zinv(const ZInvArgs &a, cudaStream_t s) {
+    cudaError_t e = cudaErrorInvalidValue;
+    ((a.n == NS ? (e = ct_launch_zinv<R, NS>(a, s), 0) : 0), ...);
+    return e;
+  }
+  static cudaError_t zfwd(const ZFwdArgs &a, cudaStream_t s) {
+    cudaError_t e = cudaErrorInvalidValue;
+    ((a.n == NS ? (e = ct_launch_zfwd<R, NS>(a, s), 0) : 0), ...);
+    return e;
+  }
+};
+
+}  // namespace gg

@@ -104,6 +104,19 @@ template <typename R> __device__ __forceinline__ R noise_cell(uint64_t seed, uin
   return lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : v[3];
 }
 
+// Periodic wrap of a coordinate into [0, L) (Eq. 3 positions).
+template <typename R>
+__device__ __forceinline__ R wrap_box(R x, R box) {
+  if (x < (R)0) x += box;
+  else if (x >= box) x -= box;
+  if (!(x >= (R)0 && x < box)) {
+    x = x - box * floor(x / box);
+    if (x >= box) x -= box;
+    if (x < (R)0) x = (R)0;
+  }
+  return x;
+}
+
 // ------------------------------------------------------------------ butterflies
 // In-register DFT of length RAD: y_k = sum_n x_n exp(-+2 pi i n k / RAD)
 // (minus sign forward, plus sign for INV).

@@ -102,6 +102,7 @@ struct ZInvArgs {
   FftStages st;           // length N/2
   const void *tw_half;
   const void *tw_full;
+  int *err;               // device error word
 };
 
 struct NoiseArgs {
@@ -116,6 +117,13 @@ template <typename R> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t s)
 template <typename R> cudaError_t launch_zinv(const ZInvArgs &a, cudaStream_t s);
 template <typename R> int max_block_threads_z(int kind, int e);  // kind 0: z forward, 2: z inverse
 template <typename R> int max_block_threads_axis(int e);
+// Size-specialised kernels (gg_ct_f32.cu / gg_ct_f64.cu) for the grid sizes of
+// the named workloads; spec_has tells whether N has them.
+template <typename R> bool spec_has(int n);
+template <typename R> int spec_axis_max_out(int n);
+template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
+template <typename R> cudaError_t spec_zinv(const ZInvArgs &a, cudaStream_t s);
+template <typename R> cudaError_t spec_zfwd(const ZFwdArgs &a, cudaStream_t s);
 cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint32_t *out,
                               cudaStream_t s);
 

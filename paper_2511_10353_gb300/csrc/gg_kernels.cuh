@@ -12,6 +12,7 @@
 #include <cudaTypedefs.h>
 
 #include "gg_device.cuh"
+#include "gg_launch.cuh"
 
 namespace gg {
 
@@ -297,18 +298,6 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
 // + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), inverse FFT of length M = N/2,
 // x_2n = Re z_n, x_2n+1 = Im z_n. Then Eq. 3 per cell: psi, pos = (q + psi)
 // mod L, vel = vfac psi; or the plain real field when pos and vel are null.
-template <typename R>
-__device__ __forceinline__ R wrap_box(R x, R box) {
-  if (x < (R)0) x += box;
-  else if (x >= box) x -= box;
-  if (!(x >= (R)0 && x < box)) {
-    x = x - box * floor(x / box);
-    if (x >= box) x -= box;
-    if (x < (R)0) x = (R)0;
-  }
-  return x;
-}
-
 template <typename R, int E>
 __global__ void k_zinv(const ZInvArgs a) {
   using C = Cx<R>;
@@ -371,12 +360,6 @@ __global__ void k_zinv(const ZInvArgs a) {
 }
 
 // ----------------------------------------------------------------- launchers
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 #define GG_DISPATCH_E(E_, ...)                 \
   switch (E_) {                                 \
     case 2: { constexpr int EE = 2; __VA_ARGS__; } break;  \
@@ -418,56 +401,6 @@ cudaError_t launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
     kern<<<blocks, threads, smem, s>>>(a);
   });
   return cudaGetLastError();
-}
-
-using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
-
-static EncodeTiledFn encode_tiled_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void *ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(ptr);
-  }
-  return fn;
-}
-
-// Tensor map of the half spectrum [N][N][N/2] complex as reals (innermost
-// 2 * N/2 reals), with a box of `cols` complex columns by rows_box points
-// along the pass axis.
-template <typename R>
-static cudaError_t make_map(CUtensorMap *m, const AxisArgs &a) {
-  EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t half = (cuuint64_t)(a.n / 2);
-  cuuint64_t dims[3] = {2 * half, (cuuint64_t)a.n, (cuuint64_t)a.n};
-  cuuint64_t strides[2] = {2 * half * sizeof(R), (cuuint64_t)a.n * 2 * half * sizeof(R)};
-  cuuint32_t box[3];
-  box[0] = (cuuint32_t)(2 * a.cols);
-  box[1] = a.axis == 1 ? (cuuint32_t)a.rows_box : 1u;
-  box[2] = a.axis == 1 ? 1u : (cuuint32_t)a.rows_box;
-  cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r =
-      fn(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
-         const_cast<void *>(a.src), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-template <typename K>
-static int persistent_blocks(K kernel, int threads, size_t smem, int64_t tiles) {
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess ||
-      per < 1)
-    per = 1;
-  const int64_t b = (int64_t)sms * per;
-  return (int)(tiles < b ? tiles : b);
 }
 
 template <typename R>
