@@ -226,6 +226,9 @@ def main():
            "pos": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)],
            "vel": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)]}
     stream = torch.cuda.current_stream()
+    t_tune = time.perf_counter()
+    variants = plan.autotune(3)  # tile variants per pass, timed on this plan's buffers
+    t_tune = time.perf_counter() - t_tune
     for i in range(max(3, args.warmup)):
         plan.zeldovich(seed=1 + i, out=out)
     plan.sync()
@@ -282,7 +285,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if w["prec"] == "f32" else "f64", "data": "synthetic",
-            "config": config_of(w), "roofline": roofline,
+            "config": dict(config_of(w), tile_variants=variants, autotune_s=round(t_tune, 3)),
+            "roofline": roofline,
             "path": {"algorithmic_bytes_per_cell": step_bytes / cells, "GB_s": path_gbs,
                      "frac_of_peak": path_gbs / peak},
             "kernels": kernels, "gpu_launches": launches, "clocks": clocks}

@@ -192,6 +192,24 @@ gg_status gg_set_profiling(gg_plan_t *plan, int enable);
 gg_status gg_profile_read(gg_plan_t *plan, int reset, int *count, const char **names, double *ms,
                           int64_t *launches, double *bytes);
 
+/* Autotuner of the transform tiles (grid sizes with size-specialised kernels:
+ * N = 64, 128, 192, 256, 384, 512, 1536 in FP32; 64, 512, 1536 in FP64).
+ * Runs the whole path `reps` times per tile variant on the plan's own buffers
+ * (allocating the component workspaces and one scratch grid for the call),
+ * times each pass with CUDA events and keeps the fastest variant per pass for
+ * later calls. Synchronous. Other sizes: returns GG_OK and changes nothing.
+ * Results do not depend on the variant (same arithmetic, different tiling). */
+gg_status gg_autotune(gg_plan_t *plan, int reps);
+
+/* The tile variant in use per pass: out[0] z forward, [1] y forward,
+ * [2] x fused, [3] y inverse (x branch), [4] y inverse (y/z branches),
+ * [5] z inverse. */
+gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]);
+
+/* Sets the tile variant per pass explicitly (same layout as gg_plan_variants;
+ * values outside 0..2 are rejected). */
+gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]);
+
 /* Wait for the plan's stream; return the first latched device error, if any. */
 gg_status gg_sync(gg_plan_t *plan);
 

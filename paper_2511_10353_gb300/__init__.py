@@ -91,6 +91,9 @@ _SIGS = {
     "gg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p]),
+    "gg_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gg_plan_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_plan_set_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gg_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gg_free": (None, [ctypes.c_void_p]),
@@ -303,6 +306,23 @@ class Plan:
 
     def sync(self):
         _check(lib().gg_sync(self._h), self._h)
+
+    def autotune(self, reps=3):
+        """Time each tile variant of the transform passes; keep the fastest per pass."""
+        self._bind_stream()
+        _check(lib().gg_autotune(self._h, int(reps)), self._h)
+        return self.variants()
+
+    def variants(self):
+        """Tile variant per pass: z fwd, y fwd, x fused, y inv (x), y inv (y/z), z inv."""
+        out = (ctypes.c_int32 * 6)()
+        _check(lib().gg_plan_variants(self._h, out), self._h)
+        return list(out)
+
+    def set_variants(self, v):
+        """Force the tile variant per pass (6 ints in 0..2)."""
+        arr = (ctypes.c_int32 * 6)(*[int(x) for x in v])
+        _check(lib().gg_plan_set_variants(self._h, arr), self._h)
 
     def set_profiling(self, on=True):
         """Bracket every launch with CUDA events on the plan's stream."""

@@ -57,6 +57,10 @@ struct gg_plan {
   gg::FftStages st_n{}, st_n_inv{}, st_half{};
   int z_lines = 1, col_b = 1;
   int col_e = 1, col_rows_box = 0;  // strided passes: elements per thread, TMA box height
+  // tile variants of the size-specialised kernels, per pass (see gg_autotune):
+  // 0 z forward, 1 y forward, 2 x fused, 3 y inverse (x branch),
+  // 4 y inverse (y/z branches), 5 z inverse
+  int variant[6] = {0, 0, 0, 0, 0, 0};
   std::string last_error;
   // host-buffer entry point: device staging of two components, a copy stream
   void *stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -277,9 +281,11 @@ void release(gg_plan_t *plan) {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // ------------------------------------------------------------ kernel timing
-enum Kind { kZFwd = 0, kYFwd, kXFused, kYInv, kZInv, kNoise, kNumKinds };
-const char *const kKindNames[kNumKinds] = {"z_forward_noise", "y_forward", "x_fused_filter",
-                                           "y_inverse", "z_inverse_epilogue", "noise"};
+enum Kind { kZFwd = 0, kYFwd, kXFused, kYInvX, kYInvYZ, kZInv, kNoise, kNumKinds };
+const char *const kKindNames[kNumKinds] = {"z_forward_noise", "y_forward",
+                                           "x_fused_filter",  "y_inverse_x",
+                                           "y_inverse_yz",    "z_inverse_epilogue",
+                                           "noise"};
 
 // Records a start event before a launch and an end event after it when the
 // plan's profiling is on; `bytes` is the launch's algorithmic HBM traffic.
@@ -331,7 +337,7 @@ template <typename R>
 gg_status launch_axis_timed(gg_plan_t *plan, const gg::AxisArgs &c, int kind, const char *what) {
   const double cb = (double)plan->cells * sizeof(R);
   const bool spec = gg::spec_has<R>(c.n);
-  const int max_out = spec ? gg::spec_axis_max_out<R>(c.n) : 3;
+  const int max_out = spec ? gg::spec_axis_max_out<R>(c.n, c.variant) : 3;
   if (c.inv && c.nout > max_out) {
     int order[3] = {0, 1, 2};
     if (c.nout == 2 && c.dst[0] == c.src) std::swap(order[0], order[1]);
@@ -368,6 +374,7 @@ gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
   z.st = plan->st_half;
   z.tw_half = plan->tab.tw_half;
   z.tw_full = plan->tab.tw_n;
+  z.variant = plan->variant[0];
   const double cb = (double)plan->cells * sizeof(R);
   cudaError_t e;
   {
@@ -381,6 +388,7 @@ gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
   c.nout = 1;
   c.dst[0] = plan->work;
   c.mul[0] = gg::kMulNone;
+  c.variant = plan->variant[1];
   return launch_axis_timed<R>(plan, c, kYFwd, "y forward pass");
 }
 
@@ -406,6 +414,7 @@ gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void 
   z.tw_half = plan->tab.tw_half;
   z.tw_full = plan->tab.tw_n;
   z.err = plan->err;
+  z.variant = plan->variant[5];
   const double cb = (double)plan->cells * sizeof(R);
   const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
   cudaError_t e;
@@ -461,6 +470,7 @@ gg_status spectral_passes(gg_plan_t *plan, uint64_t seed, const void *noise, con
     x.dst[x.nout] = buf_b;
     x.mul[x.nout++] = gg::kMulNone;
   }
+  x.variant = plan->variant[2];
   if ((st = launch_axis_timed<R>(plan, x, kXFused, "x fused pass")) != GG_OK) return st;
   if (want[0]) {
     gg::AxisArgs y = axis_args<R>(plan, 1, plan->work);
@@ -468,7 +478,8 @@ gg_status spectral_passes(gg_plan_t *plan, uint64_t seed, const void *noise, con
     y.nout = 1;
     y.dst[0] = plan->work;
     y.mul[0] = gg::kMulNone;
-    if ((st = launch_axis_timed<R>(plan, y, kYInv, "y inverse pass (x branch)")) != GG_OK) return st;
+    y.variant = plan->variant[3];
+    if ((st = launch_axis_timed<R>(plan, y, kYInvX, "y inverse pass (x branch)")) != GG_OK) return st;
   }
   if (want[1] || want[2]) {
     gg::AxisArgs y = axis_args<R>(plan, 1, buf_b);
@@ -482,7 +493,8 @@ gg_status spectral_passes(gg_plan_t *plan, uint64_t seed, const void *noise, con
       y.dst[y.nout] = buf_z;
       y.mul[y.nout++] = gg::kMulNone;
     }
-    if ((st = launch_axis_timed<R>(plan, y, kYInv, "y inverse pass (y/z branches)")) != GG_OK)
+    y.variant = plan->variant[4];
+    if ((st = launch_axis_timed<R>(plan, y, kYInvYZ, "y inverse pass (y/z branches)")) != GG_OK)
       return st;
   }
   src[0] = want[0] ? plan->work : nullptr;
@@ -522,13 +534,15 @@ gg_status run_density(gg_plan_t *plan, uint64_t seed, const void *noise, void *d
   x.nout = 1;
   x.dst[0] = plan->work;
   x.mul[0] = gg::kMulNone;
+  x.variant = plan->variant[2];
   if ((st = launch_axis_timed<R>(plan, x, kXFused, "x fused pass")) != GG_OK) return st;
   gg::AxisArgs y = axis_args<R>(plan, 1, plan->work);
   y.inv = 1;
   y.nout = 1;
   y.dst[0] = plan->work;
   y.mul[0] = gg::kMulNone;
-  if ((st = launch_axis_timed<R>(plan, y, kYInv, "y inverse pass")) != GG_OK) return st;
+  y.variant = plan->variant[3];
+  if ((st = launch_axis_timed<R>(plan, y, kYInvX, "y inverse pass")) != GG_OK) return st;
   return zinv_pass<R>(plan, 0, plan->work, delta, nullptr, nullptr, false);
 }
 
@@ -615,6 +629,66 @@ gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void 
       (e = cudaStreamSynchronize(plan->stream)) != cudaSuccess)
     return cuda_fail(plan, e, "synchronize");
   return GG_OK;
+}
+
+// Times every tile variant of the size-specialised kernels on the plan's own
+// buffers and keeps the fastest per pass. All passes are switched to variant v
+// together and timed one by one through the per-kernel events; the pass ->
+// kind map below picks each pass's time.
+template <typename R>
+gg_status autotune(gg_plan_t *plan, int reps) {
+  if (!gg::spec_has<R>((int)plan->p.n)) return GG_OK;
+  gg_status st;
+  if ((st = ensure_grid(plan, &plan->work2)) != GG_OK) return st;
+  if ((st = ensure_grid(plan, &plan->work3)) != GG_OK) return st;
+  void *tmp = nullptr;
+  if ((st = ensure_grid(plan, &tmp)) != GG_OK) return st;
+  const size_t grid = (size_t)plan->cells * sizeof(R);
+  cudaMemsetAsync(plan->work, 0, grid, plan->stream);
+  const int kinds[6] = {kZFwd, kYFwd, kXFused, kYInvX, kYInvYZ, kZInv};
+  const int nvar[6] = {gg::kSpecZVariants,    gg::kSpecAxisVariants, gg::kSpecAxisVariants,
+                       gg::kSpecAxisVariants, gg::kSpecAxisVariants, gg::kSpecZVariants};
+  double best[6];
+  int best_v[6];
+  for (int i = 0; i < 6; ++i) {
+    best[i] = 1e300;
+    best_v[i] = 0;
+  }
+  const bool prof_was = plan->prof_on;
+  void *vel[3] = {tmp, tmp, tmp};
+  for (int v = 0; v < 3; ++v) {
+    for (int i = 0; i < 6; ++i) plan->variant[i] = v < nvar[i] ? v : 0;
+    plan->prof_on = false;
+    if ((st = run_zeldovich<R>(plan, 1, nullptr, nullptr, nullptr, vel)) != GG_OK) break;  // warm
+    plan->prof_on = true;
+    for (int k = 0; k < kNumKinds; ++k) {
+      plan->prof_ms[k] = 0;
+      plan->prof_launches[k] = 0;
+    }
+    plan->prof_used = 0;
+    for (int r = 0; r < reps && st == GG_OK; ++r)
+      st = run_zeldovich<R>(plan, 1 + r, nullptr, nullptr, nullptr, vel);
+    if (st != GG_OK) break;
+    int cnt = kNumKinds;
+    if ((st = gg_profile_read(plan, 0, &cnt, nullptr, nullptr, nullptr, nullptr)) != GG_OK) break;
+    for (int i = 0; i < 6; ++i) {
+      if (v >= nvar[i]) continue;
+      const double ms = plan->prof_ms[kinds[i]];
+      if (ms < best[i]) {
+        best[i] = ms;
+        best_v[i] = v;
+      }
+    }
+  }
+  plan->prof_on = prof_was;
+  for (int k = 0; k < kNumKinds; ++k) {
+    plan->prof_ms[k] = 0;
+    plan->prof_launches[k] = 0;
+  }
+  cudaStreamSynchronize(plan->stream);
+  cudaFree(tmp);
+  for (int i = 0; i < 6; ++i) plan->variant[i] = best_v[i];
+  return st;
 }
 
 }  // namespace
@@ -841,6 +915,25 @@ gg_status gg_profile_read(gg_plan_t *plan, int reset, int *count, const char **n
       plan->prof_launches[k] = 0;
     }
   }
+  return GG_OK;
+}
+
+gg_status gg_autotune(gg_plan_t *plan, int reps) {
+  if (!plan || reps < 1) return fail(plan, GG_EINVAL, "plan NULL or reps < 1");
+  return plan->real_bytes == 8 ? autotune<double>(plan, reps) : autotune<float>(plan, reps);
+}
+
+gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]) {
+  if (!plan || !out) return fail(nullptr, GG_EINVAL, "plan or out is NULL");
+  for (int i = 0; i < 6; ++i) out[i] = plan->variant[i];
+  return GG_OK;
+}
+
+gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]) {
+  if (!plan || !v) return fail(plan, GG_EINVAL, "plan or v is NULL");
+  for (int i = 0; i < 6; ++i)
+    if (v[i] < 0 || v[i] > 2) return fail(plan, GG_EINVAL, "variant out of range");
+  for (int i = 0; i < 6; ++i) plan->variant[i] = v[i];
   return GG_OK;
 }
 

@@ -77,10 +77,9 @@ __device__ __forceinline__ int k_of(int p, int b) {
 // (INV = false) or inverse schedule, for the butterflies j = p + P*b of this
 // thread. ld(n) reads element n of the stage input, st(n, v) writes element n
 // of its output; with SYNC the stage runs in place in shared memory.
-template <typename R, int N, int SI, bool INV, bool SYNC, class Ld, class St>
+template <typename R, int N, int E, int SI, bool INV, bool SYNC, class Ld, class St>
 __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                       const St &st) {
-  constexpr int E = elems(N);
   constexpr int RAD = radix_of(N, SI, INV);
   constexpr int NS = ns_of(N, SI, INV);
   constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
@@ -123,22 +122,21 @@ __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const
 }
 
 // Stages FIRST .. LAST-1 in place in shared memory.
-template <typename R, int N, bool INV, int FIRST, int LAST, class Ld, class St>
+template <typename R, int N, int E, bool INV, int FIRST, int LAST, class Ld, class St>
 __device__ __forceinline__ void stages(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                        const St &st) {
   if constexpr (FIRST < LAST) {
-    stage<R, N, FIRST, INV, true>(p, tw, ld, st);
-    stages<R, N, INV, FIRST + 1, LAST>(p, tw, ld, st);
+    stage<R, N, E, FIRST, INV, true>(p, tw, ld, st);
+    stages<R, N, E, INV, FIRST + 1, LAST>(p, tw, ld, st);
   }
 }
 
 // The last stage of a schedule, outputs kept in registers: on return v holds
 // element j + r*N/RAD at v[b*RAD + r] (j = p + P*b).
-template <typename R, int N, bool INV, class Ld>
+template <typename R, int N, int E, bool INV, class Ld>
 __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                                 Cx<R> *v) {
   constexpr int S = nstages(N);
-  constexpr int E = elems(N);
   constexpr int RAD = radix_of(N, S - 1, INV);
   constexpr int NS = ns_of(N, S - 1, INV);
   constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
@@ -172,32 +170,39 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
 }
 
 // ------------------------------------------------------------ tile policy
-// Strided passes: columns per tile (rows of 128 bytes where two tiles fit in
-// shared memory and the CTA stays within 512 threads) and whether the spectrum
-// of two outputs may stay in registers (E <= 16 complex values per thread
-// under 128 registers; larger E runs one output per launch).
-template <typename R, int N> struct AxisPolicy {
-  static constexpr int E = elems(N);
-  static constexpr int P = N / E;
+// Tile variants the autotuner chooses between (V = 0, 1, 2 for the strided
+// pass; V = 0, 1 for the z passes). An invalid variant for a size falls back
+// to variant 0's shape.
+//
+// Strided pass, variant
+//   0: E = lcm of the radices, rows of up to 128 bytes, <= 512 threads
+//   1: E doubled (two butterflies per thread and stage), rows of up to 128 bytes
+//   2: E doubled, rows halved (a smaller CTA; several CTAs share an SM)
+// Whether the handed-off spectrum of two outputs may stay in registers is
+// estimated from the register budget; otherwise one output per launch.
+template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int CB = 2 * (int)sizeof(R);
+  static constexpr int E0 = elems(N);
+  static constexpr bool DOUBLE_OK = N % (2 * E0) == 0 && 2 * E0 * ((int)sizeof(R) / 4) <= 16;
+  static constexpr int E = (V >= 1 && DOUBLE_OK) ? 2 * E0 : E0;
+  static constexpr int P = N / E;
   static constexpr int pick() {
     int b = 128 / CB;
     while (b > 1 && ((N / 2) % b != 0 || P * b > 512 || 2 * (N * b * CB) > 200 * 1024)) b /= 2;
+    if (V == 2 && DOUBLE_OK && b * CB > 32) b /= 2;
     return b;
   }
   static constexpr int B = pick();
   static constexpr int THREADS = P * B;
-  // two outputs keep the handed-off spectrum (2E words per complex word size)
-  // live beside a stage's own E values: estimate against the register budget
   static constexpr int REG_BUDGET = 65536 / THREADS < 255 ? 65536 / THREADS : 255;
   static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
   static constexpr int MAX_OUT = REG_NEED <= REG_BUDGET ? 2 : 1;
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
 };
 
-// z passes: lines per tile (~256 threads, two dense tiles + one padded tile
-// within 160 KB).
-template <typename R, int N> struct ZPolicy {
+// z passes: lines per tile, variant 0 ~256 threads (two dense tiles + one
+// padded tile within 160 KB), variant 1 half as many lines.
+template <typename R, int N, int V> struct ZPolicy {
   static constexpr int M = N / 2;
   static constexpr int E = elems(M);
   static constexpr int P = M / E;
@@ -206,6 +211,7 @@ template <typename R, int N> struct ZPolicy {
   static constexpr int pick() {
     int l = 1;
     while (l < 64 && P * l * 2 <= 256 && (2 * (2 * l) * M + 2 * l * LD) * CB <= 160 * 1024) l *= 2;
+    if (V == 1 && l > 1) l /= 2;
     return l;
   }
   static constexpr int L = pick();

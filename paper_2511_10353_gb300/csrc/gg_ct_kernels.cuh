@@ -16,11 +16,11 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // persistent CTAs, TMA double buffering, forward stages in place in shared
 // memory, the spectrum handed to the inverse stages in registers, each
 // inverse's last stage storing straight to HBM.
-template <typename R, int N>
-__global__ void __launch_bounds__(ct::AxisPolicy<R, N>::THREADS, 1)
+template <typename R, int N, int V>
+__global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
     k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
   using C = Cx<R>;
-  using Pol = ct::AxisPolicy<R, N>;
+  using Pol = ct::AxisPolicy<R, N, V>;
   constexpr int B = Pol::B, E = Pol::E, P = Pol::P, HALF = N / 2, S = ct::nstages(N);
   constexpr int TILE = N * B;
   constexpr int TILE_STRIDE = (int)(((TILE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N>::THREADS, 1)
     auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
     C V[E];
     if (a.fwd) {
-      ct::stages<R, N, false, 0, S - 1>(p, tw, ld_smem, st_smem);
-      ct::last_stage_regs<R, N, false>(p, tw, ld_smem, V);
+      ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
+      ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, V);
     } else {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N>::THREADS, 1)
 #pragma unroll
           for (int r = 0; r < RH; ++r) buf[((p + P * b) * RH + r) * B + c] = W[b * RH + r];
         __syncthreads();
-        ct::stages<R, N, true, 1, S - 1>(p, tw, ld_smem, st_smem);
-        ct::stage<R, N, S - 1, true, false>(p, tw, ld_smem, st_glob);
+        ct::stages<R, N, E, true, 1, S - 1>(p, tw, ld_smem, st_smem);
+        ct::stage<R, N, E, S - 1, true, false>(p, tw, ld_smem, st_glob);
       }
     }
     __syncthreads();
@@ -167,10 +167,10 @@ template <int LD> __device__ __forceinline__ int zpad(int l, int n) { return l *
 // buffer while the CTA works on the current one. The c2r pre-processing reads
 // the dense buffer and writes the padded work tile; the transform runs there;
 // the last stage's outputs (natural order) feed the epilogue from registers.
-template <typename R, int N>
-__global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zinv_ct(const ZInvArgs a) {
+template <typename R, int N, int V>
+__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(const ZInvArgs a) {
   using C = Cx<R>;
-  using Pol = ct::ZPolicy<R, N>;
+  using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
   constexpr int S = ct::nstages(M);
   constexpr int RL = ct::radix_of(M, S - 1, true), SPANL = M / RL, NBL = E / RL;
@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zinv_ct(const
     __syncthreads();
     auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
     auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
-    ct::stages<R, M, true, 0, S - 1>(p, tw_half, ld_w, st_w);
+    ct::stages<R, M, E, true, 0, S - 1>(p, tw_half, ld_w, st_w);
     C v[E];
-    ct::last_stage_regs<R, M, true>(p, tw_half, ld_w, v);
+    ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
     const int64_t line = t * L + l;
     const int64_t ix = line / a.n, iy = line - ix * a.n;
     const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
@@ -261,10 +261,10 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zinv_ct(const
 // Forward z pass: Philox noise (or caller noise) of L lines into the padded
 // work tile, the length-N/2 transform in place, then the real-input unpacking
 // X_k = (Z_k + conj Z_{M-k})/2 - i/2 e^{-2 pi i k/N} (Z_k - conj Z_{M-k}).
-template <typename R, int N>
-__global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zfwd_ct(const ZFwdArgs a) {
+template <typename R, int N, int V>
+__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zfwd_ct(const ZFwdArgs a) {
   using C = Cx<R>;
-  using Pol = ct::ZPolicy<R, N>;
+  using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
   constexpr int S = ct::nstages(M);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zfwd_ct(const
     __syncthreads();
     auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
     auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
-    ct::stages<R, M, false, 0, S>(p, tw_half, ld_w, st_w);
+    ct::stages<R, M, E, false, 0, S>(p, tw_half, ld_w, st_w);
     C *dst = reinterpret_cast<C *>(a.out) + line * M;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -312,9 +312,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N>::THREADS, 1) k_zfwd_ct(const
 }
 
 // ------------------------------------------------------------ launchers
-template <typename R, int N>
+template <typename R, int N, int V>
 cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
-  using Pol = ct::AxisPolicy<R, N>;
+  using Pol = ct::AxisPolicy<R, N, V>;
   AxisArgs a = in;
   a.cols = Pol::B;
   a.inner_chunks = (N / 2) / Pol::B;
@@ -325,57 +325,70 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const size_t tile = ((size_t)N * Pol::B * 2 * sizeof(R) + 127) & ~(size_t)127;
   const size_t smem = 128 + 2 * tile;
-  auto kern = k_axis_ct<R, N>;
+  auto kern = k_axis_ct<R, N, V>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, (int64_t)N * a.inner_chunks), Pol::THREADS,
          smem, s>>>(map, a);
   return cudaGetLastError();
 }
 
-template <typename R, int N>
+template <typename R, int N, int V>
 cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
-  using Pol = ct::ZPolicy<R, N>;
+  using Pol = ct::ZPolicy<R, N, V>;
   const size_t dense = (Pol::DENSE * 2 * sizeof(R) + 127) & ~(size_t)127;
   const size_t smem = 128 + 2 * dense + (size_t)Pol::WORK * 2 * sizeof(R);
-  auto kern = k_zinv_ct<R, N>;
+  auto kern = k_zinv_ct<R, N, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, a.nlines / Pol::L), Pol::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename R, int N>
+template <typename R, int N, int V>
 cudaError_t ct_launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
-  using Pol = ct::ZPolicy<R, N>;
+  using Pol = ct::ZPolicy<R, N, V>;
   const size_t smem = (size_t)Pol::WORK * 2 * sizeof(R);
-  auto kern = k_zfwd_ct<R, N>;
+  auto kern = k_zfwd_ct<R, N, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, a.nlines / Pol::L), Pol::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Run-time dispatch over the specialised sizes. NS is a list of N values.
+constexpr int kAxisVariants = 3;
+constexpr int kZVariants = 2;
+
+// Run-time dispatch over the specialised sizes and their tile variants.
 template <typename R, int... NS> struct CtTable {
   static bool has(int n) { return ((n == NS) || ...); }
-  static int axis_max_out(int n) {
+  template <int N> static int max_out_n(int v) {
+    return v == 0 ? ct::AxisPolicy<R, N, 0>::MAX_OUT
+                  : (v == 1 ? ct::AxisPolicy<R, N, 1>::MAX_OUT : ct::AxisPolicy<R, N, 2>::MAX_OUT);
+  }
+  static int axis_max_out(int n, int v) {
     int m = 0;
-    ((m = (n == NS) ? ct::AxisPolicy<R, NS>::MAX_OUT : m), ...);
+    ((m = (n == NS) ? max_out_n<NS>(v) : m), ...);
     return m;
+  }
+  template <int N> static cudaError_t axis_n(const AxisArgs &a, cudaStream_t s) {
+    return a.variant == 1 ? ct_launch_axis<R, N, 1>(a, s)
+                          : (a.variant == 2 ? ct_launch_axis<R, N, 2>(a, s) : ct_launch_axis<R, N, 0>(a, s));
   }
   static cudaError_t axis(const AxisArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;
-    ((a.n == NS ? (e = ct_launch_axis<R, NS>(a, s), 0) : 0), ...);
+    ((a.n == NS ? (e = axis_n<NS>(a, s), 0) : 0), ...);
     return e;
   }
   static cudaError_t zinv(const ZInvArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;
-    ((a.n == NS ? (e = ct_launch_zinv<R, NS>(a, s), 0) : 0), ...);
+    ((a.n == NS ? (e = a.variant == 1 ? ct_launch_zinv<R, NS, 1>(a, s) : ct_launch_zinv<R, NS, 0>(a, s), 0)
+                : 0), ...);
     return e;
   }
   static cudaError_t zfwd(const ZFwdArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;
-    ((a.n == NS ? (e = ct_launch_zfwd<R, NS>(a, s), 0) : 0), ...);
+    ((a.n == NS ? (e = a.variant == 1 ? ct_launch_zfwd<R, NS, 1>(a, s) : ct_launch_zfwd<R, NS, 0>(a, s), 0)
+                : 0), ...);
     return e;
   }
 };

@@ -67,6 +67,7 @@ struct AxisArgs {
   int e;                  // elements per thread (multiple of every radix)
   int rows_box;           // TMA box height (divisor of N, <= 256); 0: plain loads
   int *err;               // device error word
+  int variant;            // tile variant of the size-specialised kernel
 };
 
 // Forward z pass: real lines of N (generated noise or caller noise) -> half
@@ -81,6 +82,7 @@ struct ZFwdArgs {
   FftStages st;           // length N/2
   const void *tw_half;    // exp(-2 pi i t / (N/2)), t < N/2
   const void *tw_full;    // exp(-2 pi i t / N), t < N
+  int variant;            // tile variant of the size-specialised kernel
 };
 
 // Inverse z pass (c2r) with the Zel'dovich epilogue (Eq. 3) or a plain real
@@ -103,6 +105,7 @@ struct ZInvArgs {
   const void *tw_half;
   const void *tw_full;
   int *err;               // device error word
+  int variant;            // tile variant of the size-specialised kernel
 };
 
 struct NoiseArgs {
@@ -120,7 +123,9 @@ template <typename R> int max_block_threads_axis(int e);
 // Size-specialised kernels (gg_ct_f32.cu / gg_ct_f64.cu) for the grid sizes of
 // the named workloads; spec_has tells whether N has them.
 template <typename R> bool spec_has(int n);
-template <typename R> int spec_axis_max_out(int n);
+template <typename R> int spec_axis_max_out(int n, int variant);
+constexpr int kSpecAxisVariants = 3;  // tile variants the autotuner times per strided pass
+constexpr int kSpecZVariants = 2;     // ... per z pass
 template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zinv(const ZInvArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zfwd(const ZFwdArgs &a, cudaStream_t s);
