@@ -210,6 +210,32 @@ gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]);
  * values outside 0..2 are rejected). */
 gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]);
 
+/* Largest grid (points per axis) that gg_gaussian_field_static accepts. */
+#define GG_STATIC_MAX_N 64
+
+/* The density field of gg_gaussian_field, for grids of at most
+ * GG_STATIC_MAX_N^3 cells, without any device allocation. (The paper has no
+ * counterpart: this is a calling convention of this library.)
+ *
+ * For callers that cannot call cudaMalloc: e.g. an application whose device
+ * memory is all owned by its own pool allocator, or code that must not incur
+ * cudaMalloc's implicit synchronisation. Instead of a plan's workspace, the
+ * call uses fixed arrays in the library's device image (about 2.2 MB per GPU
+ * that loads the library, held until the process exits). The caller still
+ * passes the input (noise_dev: N^3 reals of the precision in *p, or NULL to
+ * generate Philox noise from `seed`) and the output (delta_dev: N^3 reals),
+ * both 16-byte aligned device memory; `stream` is a cudaStream_t (NULL = the
+ * legacy default stream). Synchronous: returns after the result is written.
+ *
+ * All calls on one device share those arrays: calls whose work overlaps on
+ * the GPU race and corrupt each other's results, so serialise them. The
+ * first call on each device sets the arrays' device addresses up (it may load
+ * the library's device code); make it before any stream capture.
+ * n > GG_STATIC_MAX_N returns GG_EINVAL with a message in gg_last_error(NULL);
+ * invalid parameters as in gg_plan. */
+gg_status gg_gaussian_field_static(const gg_params *p, uint64_t seed, const void *noise_dev,
+                                   void *delta_dev, void *stream);
+
 /* Wait for the plan's stream; return the first latched device error, if any. */
 gg_status gg_sync(gg_plan_t *plan);
 

@@ -29,6 +29,7 @@ SOURCES = [
     "gg_kernels_f32.cu",
     "gg_kernels_f64.cu",
     "gg_kernels_common.cu",
+    "gg_static.cu",
     "gg_api.cpp",
     "gg_cosmo.cpp",
 ]

@@ -724,6 +724,8 @@ bool make_stages(int len, FftStages *st) {
   return true;
 }
 
+void set_thread_error(const char *msg) { g_thread_error = msg ? msg : ""; }
+
 FftStages reversed_stages(const FftStages &f) {
   FftStages st;
   std::memset(&st, 0, sizeof(st));

@@ -129,6 +129,8 @@ constexpr int kSpecZVariants = 2;     // ... per z pass
 template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zinv(const ZInvArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zfwd(const ZFwdArgs &a, cudaStream_t s);
+// Message returned by gg_last_error(NULL) on this host thread.
+void set_thread_error(const char *msg);
 cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint32_t *out,
                               cudaStream_t s);
 
