@@ -37,12 +37,15 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per launch of the dominant kernel from one ncu
 # capture, scaled to the bench workload, with the hash of the kernel sources it
 # was taken on; reported as null when the sources have changed since.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/x_fused_512_fp32_ncu.md: 556.1 MB read + 1019.7 MB written
+    ("x_fused_filter", "zeldovich_512_fp32"): (1575779328.0, "7e5677d7305ac251"),
+}
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gg_device.cuh", "gg_kernels.cuh"):
+    for f in ("gg_device.cuh", "gg_kernels.cuh", "gg_ct.cuh", "gg_ct_kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2511_10353_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -58,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default=None,
+                    help="comma list of 6 tile variants instead of autotuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -227,7 +232,11 @@ def main():
            "vel": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)]}
     stream = torch.cuda.current_stream()
     t_tune = time.perf_counter()
-    variants = plan.autotune(3)  # tile variants per pass, timed on this plan's buffers
+    if args.variants:
+        plan.set_variants([int(v) for v in args.variants.split(",")])
+        variants = plan.variants()
+    else:
+        variants = plan.autotune(3)  # tile variants per pass, timed on this plan's buffers
     t_tune = time.perf_counter() - t_tune
     for i in range(max(3, args.warmup)):
         plan.zeldovich(seed=1 + i, out=out)
