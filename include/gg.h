@@ -210,6 +210,44 @@ gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]);
  * values outside 0..2 are rejected). */
 gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]);
 
+/* ---------------------------------------------------------------- batched form
+ * Many independent realizations (each its own gg_params; seeds given per run)
+ * in one set of launches. Realizations with identical parameters form a
+ * group with one contiguous workspace; every pass of a group runs as one
+ * persistent launch over all its realizations (tile -> realization, tile),
+ * the groups run on forked streams, and the whole launch sequence is captured
+ * into one CUDA graph on the first gg_batch_run and replayed afterwards (seeds
+ * and output pointers are refreshed through captured copies from pinned host
+ * staging). Noise of realization r is that of a solo gg_zeldovich with
+ * seeds[r]: results equal the solo runs. */
+typedef struct gg_batch gg_batch_t;
+
+/* Plan `count` realizations (params[i], host array) on the current device;
+ * `stream` as in gg_plan. Allocates each group's workspace (3 grids per
+ * realization) and tables. */
+gg_status gg_batch_plan(gg_batch_t **batch, const gg_params *params, int count, void *stream);
+
+/* Autotune every group's tiles (as gg_autotune; synchronous). Call before
+ * the first gg_batch_run (a captured graph keeps the tiles it was captured
+ * with; autotuning afterwards drops the graph). */
+gg_status gg_batch_autotune(gg_batch_t *batch, int reps);
+
+/* Run all realizations: seeds[count] (host); psi/pos/vel are host arrays of
+ * 3*count device pointers (entry 3*i + j: component j of realization i, N_i^3
+ * reals; NULL skips that output; the arrays themselves may be NULL). The set
+ * of non-NULL outputs must be the same on every call (else the graph is
+ * captured again). Asynchronous on the batch's stream; gg_batch_sync waits. */
+gg_status gg_batch_run(gg_batch_t *batch, const uint64_t *seeds, void *const *psi,
+                       void *const *pos, void *const *vel);
+
+/* Wait for the last gg_batch_run; return the first device error. */
+gg_status gg_batch_sync(gg_batch_t *batch);
+
+/* Number of groups and total cells of the batch. */
+gg_status gg_batch_info(const gg_batch_t *batch, int *groups, int64_t *cells);
+
+void gg_batch_free(gg_batch_t *batch);
+
 /* Largest grid (points per axis) that gg_gaussian_field_static accepts. */
 #define GG_STATIC_MAX_N 64
 

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import workloads  # noqa: F401  (plain parameter dicts)
 
-__all__ = ["Plan", "GGError", "noise_bits", "cosmo_eval", "power", "filter_table",
+__all__ = ["Plan", "Batch", "GGError", "noise_bits", "cosmo_eval", "power", "filter_table",
            "workspace_size", "library_path", "lib", "workloads"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -94,6 +94,15 @@ _SIGS = {
     "gg_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gg_plan_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gg_plan_set_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_batch_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p]),
+    "gg_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gg_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "gg_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int64)]),
+    "gg_batch_free": (None, [ctypes.c_void_p]),
     "gg_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gg_free": (None, [ctypes.c_void_p]),
@@ -344,6 +353,77 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             lib().gg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many realizations (each a workload dict with n, box, cosmo, z_init, prec)
+    run as one CUDA graph of batched persistent launches (gg_batch_*)."""
+
+    def __init__(self, specs):
+        torch = _torch()
+        self.torch = torch
+        self.specs = list(specs)
+        self.count = len(self.specs)
+        arr = (Params * self.count)()
+        self._keep = []
+        for i, w in enumerate(self.specs):
+            p, keep = make_params(w["n"], w["box"], w["cosmo"], w["z_init"], w.get("prec", "f32"))
+            arr[i] = p
+            self._keep.append(keep)
+        self.stream = torch.cuda.Stream()  # graph capture needs a non-default stream
+        h = ctypes.c_void_p()
+        _check(lib().gg_batch_plan(ctypes.byref(h), arr, self.count,
+                                   ctypes.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        g = ctypes.c_int()
+        c = ctypes.c_int64()
+        _check(lib().gg_batch_info(self._h, ctypes.byref(g), ctypes.byref(c)))
+        self.groups, self.cells = g.value, c.value
+
+    def dtype(self, i):
+        return self.torch.float64 if self.specs[i].get("prec") == "f64" else self.torch.float32
+
+    def empty_outputs(self, psi=False, pos=True, vel=True):
+        t = self.torch
+        def mk(i):
+            n = self.specs[i]["n"]
+            return t.empty((n, n, n), dtype=self.dtype(i), device="cuda")
+        return {k: [[mk(i) for _ in range(3)] if want else [None] * 3 for i in range(self.count)]
+                for k, want in (("psi", psi), ("pos", pos), ("vel", vel))}
+
+    def autotune(self, reps=2):
+        _check(lib().gg_batch_autotune(self._h, int(reps)))
+
+    def run(self, seeds, out):
+        """out: dict psi/pos/vel -> list (per realization) of 3 tensors or None."""
+        seeds_arr = (ctypes.c_uint64 * self.count)(*[int(x) for x in seeds])
+        arrs = []
+        for k in ("psi", "pos", "vel"):
+            ptrs = []
+            for i in range(self.count):
+                n = self.specs[i]["n"]
+                for j in range(3):
+                    tns = out[k][i][j] if out.get(k) is not None else None
+                    ptrs.append(_dev_ptr(tns, self.dtype(i), n ** 3) if tns is not None else None)
+            arrs.append((ctypes.c_void_p * (3 * self.count))(*ptrs))
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        _check(lib().gg_batch_run(self._h, seeds_arr, *arrs))
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+        return out
+
+    def sync(self):
+        _check(lib().gg_batch_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gg_batch_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -77,6 +77,29 @@ struct gg_plan {
   double prof_bytes[16] = {0};
 };
 
+struct gg_batch {
+  struct Group {
+    gg_plan_t *plan = nullptr;          // tables, tiles and variants of the group
+    std::vector<int> members;           // batch indices of its realizations
+    void *work[3] = {nullptr, nullptr, nullptr};  // nb grids each: x, y, z branches
+    uint64_t *d_seeds = nullptr;        // device [nb]
+    void **d_lists = nullptr;           // device [3 outputs][3 components][nb]
+    uint64_t *h_seeds = nullptr;        // pinned staging of the same
+    void **h_lists = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+  };
+  int count = 0;
+  int64_t cells = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Group> groups;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t signature = 0;  // which (output, component) pairs the graph writes
+  bool ran = false;
+};
+
 namespace {
 
 gg_status fail(gg_plan_t *plan, gg_status st, const std::string &msg) {
@@ -691,6 +714,143 @@ gg_status autotune(gg_plan_t *plan, int reps) {
   return st;
 }
 
+// ------------------------------------------------------------ batched form
+bool same_params(const gg_params &a, const gg_params &b) {
+  auto eq = [](double x, double y) { return x == y || (std::isnan(x) && std::isnan(y)); };
+  const gg_cosmo &c = a.cosmo, &d = b.cosmo;
+  return a.n == b.n && eq(a.box, b.box) && a.prec == b.prec && a.flags == b.flags &&
+         eq(a.z_init, b.z_init) && eq(a.growth_override[0], b.growth_override[0]) &&
+         eq(a.growth_override[1], b.growth_override[1]) && eq(c.omega_m, d.omega_m) &&
+         eq(c.omega_l, d.omega_l) && eq(c.omega_b, d.omega_b) && eq(c.h, d.h) && eq(c.n_s, d.n_s) &&
+         eq(c.sigma_8, d.sigma_8) && eq(c.t_cmb, d.t_cmb) && c.tf == d.tf && c.tab_k == d.tab_k &&
+         c.tab_p == d.tab_p && c.tab_n == d.tab_n;
+}
+
+// All passes of one group, on stream s, every launch covering all nb
+// realizations (captured into the batch's graph).
+template <typename R>
+gg_status group_passes(gg_batch::Group &g, cudaStream_t s, uint32_t sig) {
+  gg_plan_t *plan = g.plan;
+  const cudaStream_t saved = plan->stream;
+  plan->stream = s;
+  const int n = (int)plan->p.n, half = n / 2;
+  const int nb = (int)g.members.size();
+  const int64_t grid_c = (int64_t)n * n * half;  // complex values per realization
+  gg_status st = GG_OK;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(g.d_seeds, g.h_seeds, sizeof(uint64_t) * nb, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(g.d_lists, g.h_lists, sizeof(void *) * 9 * nb, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess) {
+    plan->stream = saved;
+    return cuda_fail(nullptr, e, "batch staging copies");
+  }
+  do {
+    gg::ZFwdArgs z{};
+    z.out = g.work[0];
+    z.nlines = (int64_t)nb * n * n;
+    z.lines_per_real = (int64_t)n * n;
+    z.seeds = g.d_seeds;
+    z.n = n;
+    z.lines_per_cta = plan->z_lines;
+    z.st = plan->st_half;
+    z.tw_half = plan->tab.tw_half;
+    z.tw_full = plan->tab.tw_n;
+    z.variant = plan->variant[0];
+    e = gg::spec_has<R>(n) ? gg::spec_zfwd<R>(z, s) : gg::launch_zfwd<R>(z, s);
+    if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "batched z forward"); break; }
+    auto ax = [&](const void *src) {
+      gg::AxisArgs c = axis_args<R>(plan, 1, src);
+      c.nbatch = nb;
+      c.batch_stride = grid_c;
+      return c;
+    };
+    gg::AxisArgs y = ax(g.work[0]);
+    y.fwd = 1;
+    y.nout = 1;
+    y.dst[0] = g.work[0];
+    y.variant = plan->variant[1];
+    if ((st = launch_axis_timed<R>(plan, y, kYFwd, "batched y forward")) != GG_OK) break;
+    gg::AxisArgs x = ax(g.work[0]);
+    x.axis = 0;
+    x.stride = (int64_t)n * half;
+    x.outer_stride = half;
+    x.fwd = 1;
+    x.inv = 1;
+    x.pre = 1;
+    x.table = plan->tab.u_phi;
+    x.nout = 2;
+    x.dst[0] = g.work[0];
+    x.mul[0] = gg::kMulIm;
+    x.dst[1] = g.work[1];
+    x.mul[1] = gg::kMulNone;
+    x.variant = plan->variant[2];
+    if ((st = launch_axis_timed<R>(plan, x, kXFused, "batched x fused")) != GG_OK) break;
+    gg::AxisArgs ya = ax(g.work[0]);
+    ya.inv = 1;
+    ya.nout = 1;
+    ya.dst[0] = g.work[0];
+    ya.variant = plan->variant[3];
+    if ((st = launch_axis_timed<R>(plan, ya, kYInvX, "batched y inverse (x)")) != GG_OK) break;
+    gg::AxisArgs yb = ax(g.work[1]);
+    yb.inv = 1;
+    yb.nout = 2;
+    yb.dst[0] = g.work[1];
+    yb.mul[0] = gg::kMulIm;
+    yb.dst[1] = g.work[2];
+    yb.mul[1] = gg::kMulNone;
+    yb.variant = plan->variant[4];
+    if ((st = launch_axis_timed<R>(plan, yb, kYInvYZ, "batched y inverse (y/z)")) != GG_OK) break;
+    for (int j = 0; j < 3 && st == GG_OK; ++j) {
+      const bool any = (sig >> j) & 0x49;  // psi_j, pos_j or vel_j wanted anywhere
+      if (!any) continue;
+      gg::ZInvArgs zi{};
+      zi.src = g.work[j];
+      zi.nlines = (int64_t)nb * n * n;
+      zi.lines_per_real = (int64_t)n * n;
+      zi.psi_list = ((sig >> (0 * 3 + j)) & 1) ? g.d_lists + (0 * 3 + j) * nb : nullptr;
+      zi.pos_list = ((sig >> (1 * 3 + j)) & 1) ? g.d_lists + (1 * 3 + j) * nb : nullptr;
+      zi.vel_list = ((sig >> (2 * 3 + j)) & 1) ? g.d_lists + (2 * 3 + j) * nb : nullptr;
+      zi.n = n;
+      zi.lines_per_cta = plan->z_lines;
+      zi.comp = j;
+      zi.mul_kz = j == 2;
+      zi.box = plan->p.box;
+      zi.cell = plan->p.box / (double)n;
+      zi.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
+      zi.vfac = plan->info.vfac;
+      zi.st = plan->st_half;
+      zi.tw_half = plan->tab.tw_half;
+      zi.tw_full = plan->tab.tw_n;
+      zi.err = plan->err;
+      zi.variant = plan->variant[5];
+      e = gg::spec_has<R>(n) ? gg::spec_zinv<R>(zi, s) : gg::launch_zinv<R>(zi, s);
+      if (e != cudaSuccess) st = cuda_fail(nullptr, e, "batched z inverse");
+    }
+  } while (false);
+  plan->stream = saved;
+  return st;
+}
+
+void batch_release(gg_batch_t *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto &g : b->groups) {
+    for (void *w : g.work)
+      if (w) cudaFree(w);
+    if (g.d_seeds) cudaFree(g.d_seeds);
+    if (g.d_lists) cudaFree(g.d_lists);
+    if (g.h_seeds) cudaFreeHost(g.h_seeds);
+    if (g.h_lists) cudaFreeHost(g.h_lists);
+    if (g.ev) cudaEventDestroy(g.ev);
+    if (g.s) cudaStreamDestroy(g.s);
+    if (g.plan) gg_free(g.plan);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+}
+
 }  // namespace
 
 namespace gg {
@@ -961,6 +1121,166 @@ void gg_free(gg_plan_t *plan) {
   if (!plan) return;
   release(plan);
   delete plan;
+}
+
+gg_status gg_batch_plan(gg_batch_t **batch, const gg_params *params, int count, void *stream) {
+  if (!batch || !params || count < 1) return fail(nullptr, GG_EINVAL, "bad batch arguments");
+  *batch = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const std::string msg = validate(&params[i]);
+    if (!msg.empty()) return fail(nullptr, GG_EINVAL, "realization " + std::to_string(i) + ": " + msg);
+  }
+  gg_batch_t *b = new (std::nothrow) gg_batch_t();
+  if (!b) return fail(nullptr, GG_ENOMEM, "host allocation failed");
+  b->count = count;
+  b->stream = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    b->cells += params[i].n * params[i].n * params[i].n;
+    size_t gi = 0;
+    for (; gi < b->groups.size(); ++gi)
+      if (same_params(params[b->groups[gi].members[0]], params[i])) break;
+    if (gi == b->groups.size()) b->groups.emplace_back();
+    b->groups[gi].members.push_back(i);
+  }
+  gg_status st = GG_OK;
+  cudaError_t e = cudaSuccess;
+  for (auto &g : b->groups) {
+    const gg_params &p = params[g.members[0]];
+    if ((st = gg_plan(&g.plan, &p, stream)) != GG_OK) break;
+    const size_t nb = g.members.size();
+    const size_t bytes = (size_t)p.n * p.n * p.n * (p.prec == GG_F64 ? 8 : 4) * nb;
+    for (void *&w : g.work)
+      if (cudaMalloc(&w, bytes) != cudaSuccess) st = fail(nullptr, GG_ENOMEM, "cudaMalloc of a batch workspace failed");
+    if (st != GG_OK) break;
+    if ((e = cudaMalloc(&g.d_seeds, sizeof(uint64_t) * nb)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&g.d_lists, sizeof(void *) * 9 * nb)) != cudaSuccess ||
+        (e = cudaMallocHost(&g.h_seeds, sizeof(uint64_t) * nb)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&g.h_lists, sizeof(void *) * 9 * nb)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming)) != cudaSuccess) {
+      st = cuda_fail(nullptr, e, "batch set-up");
+      break;
+    }
+  }
+  if (st == GG_OK && ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+                      (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess))
+    st = cuda_fail(nullptr, e, "batch events");
+  if (st != GG_OK) {
+    batch_release(b);
+    delete b;
+    return st;
+  }
+  *batch = b;
+  return GG_OK;
+}
+
+gg_status gg_batch_autotune(gg_batch_t *b, int reps) {
+  if (!b || reps < 1) return fail(nullptr, GG_EINVAL, "bad arguments");
+  for (auto &g : b->groups) {
+    g.plan->stream = b->stream;
+    const gg_status st = gg_autotune(g.plan, reps);
+    if (st != GG_OK) return fail(nullptr, st, g.plan->last_error);
+  }
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return GG_OK;
+}
+
+gg_status gg_batch_run(gg_batch_t *b, const uint64_t *seeds, void *const *psi, void *const *pos,
+                       void *const *vel) {
+  if (!b || !seeds) return fail(nullptr, GG_EINVAL, "batch or seeds is NULL");
+  cudaError_t e;
+  if (b->ran && (e = cudaEventSynchronize(b->done)) != cudaSuccess)  // staging is re-read by the graph
+    return cuda_fail(nullptr, e, "waiting for the previous batch run");
+  void *const *outs[3] = {psi, pos, vel};
+  uint32_t sig = 0;
+  for (int i = 0; i < b->count; ++i)
+    for (int o = 0; o < 3; ++o)
+      for (int j = 0; j < 3; ++j) {
+        const void *ptr = outs[o] ? outs[o][3 * i + j] : nullptr;
+        if (ptr && ((uintptr_t)ptr & 15u)) return fail(nullptr, GG_EINVAL, "output buffer unaligned");
+        if (ptr) sig |= 1u << (o * 3 + j);
+      }
+  for (auto &g : b->groups) {
+    const int nb = (int)g.members.size();
+    for (int k = 0; k < nb; ++k) {
+      const int i = g.members[k];
+      g.h_seeds[k] = seeds[i];
+      for (int o = 0; o < 3; ++o)
+        for (int j = 0; j < 3; ++j) g.h_lists[(o * 3 + j) * nb + k] = outs[o] ? outs[o][3 * i + j] : nullptr;
+    }
+  }
+  if (!b->exec || sig != b->signature) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+    }
+    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(nullptr, e, "cudaStreamBeginCapture (a batch needs a non-default stream)");
+    gg_status st = GG_OK;
+    if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) st = cuda_fail(nullptr, e, "fork");
+    for (auto &g : b->groups) {
+      if (st != GG_OK) break;
+      if ((e = cudaStreamWaitEvent(g.s, b->fork, 0)) != cudaSuccess) {
+        st = cuda_fail(nullptr, e, "fork wait");
+        break;
+      }
+      st = g.plan->real_bytes == 8 ? group_passes<double>(g, g.s, sig) : group_passes<float>(g, g.s, sig);
+      if (st != GG_OK) break;
+      if ((e = cudaEventRecord(g.ev, g.s)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(b->stream, g.ev, 0)) != cudaSuccess)
+        st = cuda_fail(nullptr, e, "join");
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    if (st != GG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ec != cudaSuccess) return cuda_fail(nullptr, ec, "cudaStreamEndCapture");
+    if ((e = cudaGraphInstantiate(&b->exec, graph, 0)) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_fail(nullptr, e, "cudaGraphInstantiate");
+    }
+    b->graph = graph;
+    b->signature = sig;
+  }
+  if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess ||
+      (e = cudaEventRecord(b->done, b->stream)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaGraphLaunch");
+  b->ran = true;
+  return GG_OK;
+}
+
+gg_status gg_batch_sync(gg_batch_t *b) {
+  if (!b) return fail(nullptr, GG_EINVAL, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaStreamSynchronize");
+  for (auto &g : b->groups) {
+    const gg_status st = gg_sync(g.plan);
+    if (st != GG_OK) return fail(nullptr, st, g.plan->last_error);
+  }
+  return GG_OK;
+}
+
+gg_status gg_batch_info(const gg_batch_t *b, int *groups, int64_t *cells) {
+  if (!b) return fail(nullptr, GG_EINVAL, "batch is NULL");
+  if (groups) *groups = (int)b->groups.size();
+  if (cells) *cells = b->cells;
+  return GG_OK;
+}
+
+void gg_batch_free(gg_batch_t *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  delete b;
 }
 
 }  // extern "C"

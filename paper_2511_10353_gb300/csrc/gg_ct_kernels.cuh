@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
   const int tid = threadIdx.x;
-  const int64_t ntiles = (int64_t)N * INNER;
+  const int64_t per_real = (int64_t)N * INNER;
+  const int64_t ntiles = per_real * (a.nbatch > 0 ? a.nbatch : 1);
   const C *tw = reinterpret_cast<const C *>(a.tw);
   const R *table = reinterpret_cast<const R *>(a.table);
   if (tid == 0) {
@@ -42,14 +43,16 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
   }
   __syncthreads();
   auto issue = [&](int64_t t, int sb) {
-    const int64_t outer = t / INNER;
-    const int chunk = (int)(t - outer * INNER);
+    const int rr = (int)(t / per_real);
+    const int64_t tt = t - rr * per_real;
+    const int64_t outer = tt / INNER;
+    const int chunk = (int)(tt - outer * INNER);
     C *dst = bufs + sb * TILE_STRIDE;
     mbar_arrive_expect_tx(&bars[sb], (uint32_t)(TILE * sizeof(C)));
 #pragma unroll
     for (int i = 0; i < N; i += Pol::ROWS_BOX) {
-      if (a.axis == 1) tma_load_3d(dst + i * B, &map, &bars[sb], chunk * B * 2, i, (int)outer);
-      else tma_load_3d(dst + i * B, &map, &bars[sb], chunk * B * 2, (int)outer, i);
+      if (a.axis == 1) tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, i, (int)outer, rr);
+      else tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, (int)outer, i, rr);
     }
   };
   int64_t t = blockIdx.x;
@@ -63,11 +66,13 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
     }
     int c = tid & (B - 1), p = tid / B;
     asm volatile("" : "+r"(c), "+r"(p));
-    const int64_t outer = t / INNER;
-    const int chunk = (int)(t - outer * INNER);
+    const int64_t rr = t / per_real;
+    const int64_t tt = t - rr * per_real;
+    const int64_t outer = tt / INNER;
+    const int chunk = (int)(tt - outer * INNER);
     const int kz = chunk * B + c;
     C *buf = bufs + sb * TILE_STRIDE;
-    const int64_t gbase = outer * a.outer_stride + kz;
+    const int64_t gbase = rr * a.batch_stride + outer * a.outer_stride + kz;
     const int m_outer = a.axis == 0 ? ct_freq((int)outer, N) : 0;
     const bool nyq_outer = a.axis == 0 && (int)outer == HALF;
     auto tab_index = [&](int n) {
@@ -232,11 +237,17 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(co
     C v[E];
     ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
     const int64_t line = t * L + l;
-    const int64_t ix = line / a.n, iy = line - ix * a.n;
+    const int64_t lpr = a.lines_per_real > 0 ? a.lines_per_real : a.nlines;
+    const int64_t rr = line / lpr, local = line - rr * lpr;
+    const int64_t ix = local / a.n, iy = local - ix * a.n;
     const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
-    C *psi = a.psi ? reinterpret_cast<C *>(a.psi) + line * M : nullptr;
-    C *pos = a.pos ? reinterpret_cast<C *>(a.pos) + line * M : nullptr;
-    C *vel = a.vel ? reinterpret_cast<C *>(a.vel) + line * M : nullptr;
+    void *psi_b = a.psi_list ? a.psi_list[rr] : a.psi;
+    void *pos_b = a.pos_list ? a.pos_list[rr] : a.pos;
+    void *vel_b = a.vel_list ? a.vel_list[rr] : a.vel;
+    const int64_t off = (a.psi_list || a.pos_list || a.vel_list) ? local * M : line * M;
+    C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
+    C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
+    C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
 #pragma unroll
     for (int b = 0; b < NBL; ++b)
 #pragma unroll
@@ -277,18 +288,21 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zfwd_ct(co
     int l = tid / P, p = tid - (tid / P) * P;
     asm volatile("" : "+r"(l), "+r"(p));
     const int64_t line = t * L + l;
+    const int64_t lpr = a.lines_per_real > 0 ? a.lines_per_real : a.nlines;
+    const int64_t rr = line / lpr, local = line - rr * lpr;
+    const uint64_t seed = a.seeds ? a.seeds[rr] : a.seed;
     if (a.noise) {
       const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
 #pragma unroll
       for (int i = 0; i < E; ++i) work[zpad<LD>(l, p + P * i)] = src[p + P * i];
     } else {
       static_assert(N % 4 == 0, "lines start on a Philox group");
-      const uint64_t g0 = (uint64_t)line * (uint64_t)(N / 4);
+      const uint64_t g0 = (uint64_t)local * (uint64_t)(N / 4);
 #pragma unroll
       for (int i = 0; i < E / 2; ++i) {
         const int q = p + P * i;
         R w[4];
-        gauss4(noise_words(a.seed, g0 + q), w);
+        gauss4(noise_words(seed, g0 + q), w);
         work[zpad<LD>(l, 2 * q)] = C{w[0], w[1]};
         work[zpad<LD>(l, 2 * q + 1)] = C{w[2], w[3]};
       }
@@ -327,8 +341,8 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   const size_t smem = 128 + 2 * tile;
   auto kern = k_axis_ct<R, N, V>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-  kern<<<persistent_blocks(kern, Pol::THREADS, smem, (int64_t)N * a.inner_chunks), Pol::THREADS,
-         smem, s>>>(map, a);
+  const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);
+  kern<<<persistent_blocks(kern, Pol::THREADS, smem, tiles), Pol::THREADS, smem, s>>>(map, a);
   return cudaGetLastError();
 }
 

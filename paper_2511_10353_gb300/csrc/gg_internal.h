@@ -68,6 +68,8 @@ struct AxisArgs {
   int rows_box;           // TMA box height (divisor of N, <= 256); 0: plain loads
   int *err;               // device error word
   int variant;            // tile variant of the size-specialised kernel
+  int nbatch;             // realizations in the buffers (<= 0 means 1), outermost
+  int64_t batch_stride;   // complex elements between realizations
 };
 
 // Forward z pass: real lines of N (generated noise or caller noise) -> half
@@ -83,6 +85,8 @@ struct ZFwdArgs {
   const void *tw_half;    // exp(-2 pi i t / (N/2)), t < N/2
   const void *tw_full;    // exp(-2 pi i t / N), t < N
   int variant;            // tile variant of the size-specialised kernel
+  const uint64_t *seeds;  // batched form: device array, one seed per realization (else seed)
+  int64_t lines_per_real; // lines of one realization (<= 0: nlines)
 };
 
 // Inverse z pass (c2r) with the Zel'dovich epilogue (Eq. 3) or a plain real
@@ -106,6 +110,10 @@ struct ZInvArgs {
   const void *tw_full;
   int *err;               // device error word
   int variant;            // tile variant of the size-specialised kernel
+  int64_t lines_per_real; // lines of one realization (<= 0: nlines)
+  void *const *psi_list;  // batched form: device arrays of per-realization outputs
+  void *const *pos_list;  // (entries may be null); when set they replace psi/pos/vel
+  void *const *vel_list;
 };
 
 struct NoiseArgs {

@@ -56,6 +56,9 @@ __global__ void k_zfwd(const ZFwdArgs a) {
   const int l = threadIdx.x / P, p = threadIdx.x - l * P;
   const int64_t line = (int64_t)blockIdx.x * a.lines_per_cta + l;
   const bool live = line < a.nlines;
+  const int64_t lpr = a.lines_per_real > 0 ? a.lines_per_real : a.nlines;
+  const int64_t rr = line / lpr, local = line - rr * lpr;  // realization, line within it
+  const uint64_t seed = (a.seeds && live) ? a.seeds[rr] : a.seed;
   if (live) {
     if (a.noise) {
       const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
@@ -63,22 +66,22 @@ __global__ void k_zfwd(const ZFwdArgs a) {
       for (int i = 0; i < E; ++i) buf[lay(l, p + P * i)] = src[p + P * i];
     } else if ((a.n & 3) == 0) {
       if constexpr (E % 2 == 0) {
-        const uint64_t g0 = (uint64_t)line * (uint64_t)(a.n >> 2);
+        const uint64_t g0 = (uint64_t)local * (uint64_t)(a.n >> 2);
 #pragma unroll
         for (int i = 0; i < E / 2; ++i) {
           const int q = p + P * i;
           R v[4];
-          gauss4(noise_words(a.seed, g0 + q), v);
+          gauss4(noise_words(seed, g0 + q), v);
           buf[lay(l, 2 * q)] = C{v[0], v[1]};
           buf[lay(l, 2 * q + 1)] = C{v[2], v[3]};
         }
       }
     } else {
-      const uint64_t c0 = (uint64_t)line * (uint64_t)a.n;
+      const uint64_t c0 = (uint64_t)local * (uint64_t)a.n;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int k = p + P * i;
-        buf[lay(l, k)] = C{noise_cell<R>(a.seed, c0 + 2 * k), noise_cell<R>(a.seed, c0 + 2 * k + 1)};
+        buf[lay(l, k)] = C{noise_cell<R>(seed, c0 + 2 * k), noise_cell<R>(seed, c0 + 2 * k + 1)};
       }
     }
   }
@@ -134,7 +137,8 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
   const int stride_elems = ((tile_elems * (int)sizeof(C) + 127) & ~127) / (int)sizeof(C);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
   const int tid = threadIdx.x;
-  const int64_t ntiles = (int64_t)N * a.inner_chunks;
+  const int64_t per_real = (int64_t)N * a.inner_chunks;
+  const int64_t ntiles = per_real * (a.nbatch > 0 ? a.nbatch : 1);
   const uint32_t tile_bytes = (uint32_t)(tile_elems * sizeof(C));
   const C *tw = reinterpret_cast<const C *>(a.tw);
   const R *table = reinterpret_cast<const R *>(a.table);
@@ -150,14 +154,16 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
   }
   __syncthreads();
   auto issue = [&](int64_t t, int sb) {
-    const int64_t outer = t / a.inner_chunks;
-    const int chunk = (int)(t - outer * a.inner_chunks);
+    const int rr = (int)(t / per_real);
+    const int64_t tt = t - rr * per_real;
+    const int64_t outer = tt / a.inner_chunks;
+    const int chunk = (int)(tt - outer * a.inner_chunks);
     C *dst = bufs + sb * stride_elems;
     mbar_arrive_expect_tx(&bars[sb], tile_bytes);
     const int c0 = chunk * B * 2;  // innermost coordinate in reals
     for (int i = 0; i < N; i += a.rows_box) {
-      if (a.axis == 1) tma_load_3d(dst + i * B, &map, &bars[sb], c0, i, (int)outer);
-      else tma_load_3d(dst + i * B, &map, &bars[sb], c0, (int)outer, i);
+      if (a.axis == 1) tma_load_4d(dst + i * B, &map, &bars[sb], c0, i, (int)outer, rr);
+      else tma_load_4d(dst + i * B, &map, &bars[sb], c0, (int)outer, i, rr);
     }
   };
   int64_t t = blockIdx.x;
@@ -175,11 +181,13 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
     // stay live for the whole kernel)
     int c = tid & (B - 1), p = tid / B;
     asm volatile("" : "+r"(c), "+r"(p));
-    const int64_t outer = t / a.inner_chunks;
-    const int chunk = (int)(t - outer * a.inner_chunks);
+    const int64_t rr = t / per_real;
+    const int64_t tt = t - rr * per_real;
+    const int64_t outer = tt / a.inner_chunks;
+    const int chunk = (int)(tt - outer * a.inner_chunks);
     const int kz = chunk * B + c;
     C *buf = bufs + sb * stride_elems;
-    const int64_t gbase = outer * a.outer_stride + kz;
+    const int64_t gbase = rr * a.batch_stride + outer * a.outer_stride + kz;
     const int m_outer = a.axis == 0 ? freq_of((int)outer, N) : 0;
     const bool nyq_outer = a.axis == 0 && (int)outer == half;
     auto ld_smem = [&](int n) { return buf[n * B + c]; };
@@ -212,7 +220,8 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
         break;
       }
     } else {
-      const C *src = reinterpret_cast<const C *>(a.src) + outer * a.outer_stride + chunk * B;
+      const C *src = reinterpret_cast<const C *>(a.src) + rr * a.batch_stride +
+                     outer * a.outer_stride + chunk * B;
       for (int q = tid; q < tile_elems; q += blockDim.x) {
         const int n = q / B;
         buf[q] = src[(int64_t)n * a.stride + (q - n * B)];
@@ -336,12 +345,18 @@ __global__ void k_zinv(const ZInvArgs a) {
   __syncthreads();
   fft_smem<R, E, true>(buf, lay, l, p, P, a.st, reinterpret_cast<const C *>(a.tw_half));
   if (!live) return;
-  const int64_t ix = line / a.n, iy = line - ix * a.n;
+  const int64_t lpr = a.lines_per_real > 0 ? a.lines_per_real : a.nlines;
+  const int64_t rr = line / lpr, local = line - rr * lpr;
+  const int64_t ix = local / a.n, iy = local - ix * a.n;
   const R box = (R)a.box, cell = (R)a.cell, qo = (R)a.q_offset, vfac = (R)a.vfac;
   const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
-  C *psi = a.psi ? reinterpret_cast<C *>(a.psi) + line * M : nullptr;
-  C *pos = a.pos ? reinterpret_cast<C *>(a.pos) + line * M : nullptr;
-  C *vel = a.vel ? reinterpret_cast<C *>(a.vel) + line * M : nullptr;
+  void *psi_b = a.psi_list ? a.psi_list[rr] : a.psi;
+  void *pos_b = a.pos_list ? a.pos_list[rr] : a.pos;
+  void *vel_b = a.vel_list ? a.vel_list[rr] : a.vel;
+  const int64_t off = (a.psi_list || a.pos_list || a.vel_list) ? local * M : line * M;
+  C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
+  C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
+  C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const int n = p + P * i;
@@ -412,7 +427,7 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t s) {
   const int P = a.n / a.e;
   const unsigned threads = (unsigned)(P * a.cols);
   const size_t smem = axis_smem_bytes(a.n, a.cols, sizeof(Cx<R>));
-  const int64_t tiles = (int64_t)a.n * a.inner_chunks;
+  const int64_t tiles = (int64_t)a.n * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);
   GG_DISPATCH_E(a.e, {
     auto kern = k_axis<R, EE>;
     if ((e = set_smem(kern, smem)) != cudaSuccess) return e;

@@ -33,23 +33,27 @@ static EncodeTiledFn encode_tiled_fn() {
   return fn;
 }
 
-// Tensor map of the half spectrum [N][N][N/2] complex as reals (innermost
-// 2 * N/2 reals), with a box of `cols` complex columns by rows_box points
-// along the pass axis.
+// Tensor map of the half spectra [nbatch][N][N][N/2] complex as reals
+// (innermost 2 * N/2 reals), with a box of `cols` complex columns by rows_box
+// points along the pass axis (one x or y index, one realization).
 template <typename R>
 static cudaError_t make_map(CUtensorMap *m, const AxisArgs &a) {
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t half = (cuuint64_t)(a.n / 2);
-  cuuint64_t dims[3] = {2 * half, (cuuint64_t)a.n, (cuuint64_t)a.n};
-  cuuint64_t strides[2] = {2 * half * sizeof(R), (cuuint64_t)a.n * 2 * half * sizeof(R)};
-  cuuint32_t box[3];
+  const cuuint64_t nb = a.nbatch > 0 ? (cuuint64_t)a.nbatch : 1;
+  const cuuint64_t bstride = a.nbatch > 1 ? (cuuint64_t)a.batch_stride * 2 * sizeof(R)
+                                          : (cuuint64_t)a.n * a.n * 2 * half * sizeof(R);
+  cuuint64_t dims[4] = {2 * half, (cuuint64_t)a.n, (cuuint64_t)a.n, nb};
+  cuuint64_t strides[3] = {2 * half * sizeof(R), (cuuint64_t)a.n * 2 * half * sizeof(R), bstride};
+  cuuint32_t box[4];
   box[0] = (cuuint32_t)(2 * a.cols);
   box[1] = a.axis == 1 ? (cuuint32_t)a.rows_box : 1u;
   box[2] = a.axis == 1 ? 1u : (cuuint32_t)a.rows_box;
-  cuuint32_t estr[3] = {1, 1, 1};
+  box[3] = 1u;
+  cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r =
-      fn(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+      fn(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
          const_cast<void *>(a.src), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -1,0 +1,86 @@
+"""The batched form: many realizations as one CUDA graph of batched launches.
+
+Every realization of a batch must equal the solo gg_zeldovich run with its
+seed, bit for bit (the noise is keyed by (seed, cell index) and the batched
+launches run the same butterflies), including after the graph is replayed
+with new seeds and output buffers. The 48-realization workload (N cycling
+128/192/256/384, L = N Mpc/h, seeds 1..48) is checked on one realization of
+each size.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BBKS = dict(omega_m=0.3, h=0.7, n_s=0.96, sigma_8=0.8, tf="bbks", omega_l=-1.0,
+            omega_b=0.049, t_cmb=2.7255)
+
+
+@pytest.fixture(scope="module")
+def gg():
+    from paper_2511_10353_gb300 import build
+    build.build(verbose=False)
+    import paper_2511_10353_gb300 as m
+    return m
+
+
+def _solo(gg, w, seed):
+    plan = gg.Plan(w["n"], w["box"], w["cosmo"], w["z_init"], w.get("prec", "f32"))
+    out = plan.zeldovich(seed=seed)
+    plan.sync()
+    res = {k: [t.cpu().numpy() for t in out[k]] for k in ("psi", "pos", "vel")}
+    plan.close()
+    return res
+
+
+def test_small_mixed_batch_equals_solo_runs(gg):
+    specs = []
+    for i, n in enumerate((32, 48, 64, 32, 48, 64, 32)):
+        specs.append(dict(n=n, box=float(n), cosmo=BBKS, z_init=50.0,
+                          prec="f64" if i == 6 else "f32"))
+    b = gg.Batch(specs)
+    assert b.groups == 4
+    out = b.empty_outputs(psi=True)
+    for seeds in ([1, 2, 3, 4, 5, 6, 7], [21, 22, 23, 24, 25, 26, 27]):
+        b.run(seeds, out)
+        b.sync()
+        for i, w in enumerate(specs):
+            want = _solo(gg, w, seeds[i])
+            for k in ("psi", "pos", "vel"):
+                for j in range(3):
+                    assert np.array_equal(out[k][i][j].cpu().numpy(), want[k][j]), (i, k, j)
+    b.close()
+
+
+def test_partial_outputs(gg):
+    specs = [dict(n=64, box=64.0, cosmo=BBKS, z_init=50.0)] * 3
+    b = gg.Batch(specs)
+    out = b.empty_outputs(psi=False, pos=True, vel=False)
+    out["pos"][1] = [None, out["pos"][1][1], None]
+    b.run([5, 6, 7], out)
+    b.sync()
+    want = _solo(gg, specs[1], 6)
+    assert np.array_equal(out["pos"][1][1].cpu().numpy(), want["pos"][1])
+    want0 = _solo(gg, specs[0], 5)
+    for j in range(3):
+        assert np.array_equal(out["pos"][0][j].cpu().numpy(), want0["pos"][j])
+    b.close()
+
+
+def test_batched_48_workload(gg):
+    from paper_2511_10353_gb300.workloads import batched_realizations
+    specs = batched_realizations()
+    b = gg.Batch(specs)
+    assert b.groups == 4 and b.cells == 12 * (128 ** 3 + 192 ** 3 + 256 ** 3 + 384 ** 3)
+    b.autotune(1)
+    out = b.empty_outputs()
+    seeds = [w["seed"] for w in specs]
+    b.run(seeds, out)
+    b.sync()
+    for i in (0, 5, 10, 47):
+        want = _solo(gg, specs[i], seeds[i])
+        for k in ("pos", "vel"):
+            for j in range(3):
+                assert np.array_equal(out[k][i][j].cpu().numpy(), want[k][j]), (i, k, j)
+    b.close()
