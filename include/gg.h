@@ -274,6 +274,34 @@ void gg_batch_free(gg_batch_t *batch);
 gg_status gg_gaussian_field_static(const gg_params *p, uint64_t seed, const void *noise_dev,
                                    void *delta_dev, void *stream);
 
+/* ---------------------------------------------------------------- adjoint form
+ * Pieces of a differentiable chain noise -> displacement -> CIC density ->
+ * smoothed density for gradient-based fitting of constrained realizations
+ * (no paper counterpart; the map W -> psi is that of Eqs. 1-2). */
+
+/* Transpose of the linear map W -> psi_j (Eqs. 1-2) applied to upstream
+ * gradients: g_noise = sum_j J_j^T g_psi[j]. Each J_j multiplies the spectrum
+ * by the purely imaginary, Hermitian i k_j D sqrt(P/V) / k^2, so J_j^T = -J_j:
+ * g_noise = -sum_j J_j g_psi[j], one forward chain per non-NULL component;
+ * no transform intermediates are stored. g_psi entries: N^3 reals or NULL;
+ * g_noise_dev: N^3 reals (overwritten). */
+gg_status gg_zeldovich_adjoint(gg_plan_t *plan, const void *const g_psi_dev[3], void *g_noise_dev);
+
+/* Gaussian smoothing out = F^-1[exp(-k^2 R^2 / 2) F in] (R in Mpc/h, modes with
+ * |m_j| = N/2 dropped); symmetric, hence its own adjoint. in may equal out. */
+gg_status gg_smooth(gg_plan_t *plan, double radius, const void *in_dev, void *out_dev);
+
+/* Cloud-in-cell density contrast of one particle per Lagrangian cell at
+ * x = q + psi (periodic): delta(c) = sum_p w_c(x_p) - 1, nodes at the cell
+ * centres, linear weights per axis. psi_dev: 3 x N^3 reals; delta_dev: N^3. */
+gg_status gg_cic_density(gg_plan_t *plan, const void *const psi_dev[3], void *delta_dev);
+
+/* Adjoint of gg_cic_density at psi: g_psi[j](p) = sum_c g_delta(c) dw_c(x_p)/dpsi_j
+ * (one-sided where a particle sits exactly on a node plane). NULL entries of
+ * g_psi_dev are skipped. */
+gg_status gg_cic_density_adjoint(gg_plan_t *plan, const void *const psi_dev[3],
+                                 const void *g_delta_dev, void *const g_psi_dev[3]);
+
 /* Wait for the plan's stream; return the first latched device error, if any. */
 gg_status gg_sync(gg_plan_t *plan);
 

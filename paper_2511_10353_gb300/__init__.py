@@ -103,6 +103,11 @@ _SIGS = {
     "gg_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int64)]),
     "gg_batch_free": (None, [ctypes.c_void_p]),
+    "gg_zeldovich_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_smooth": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_cic_density_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
     "gg_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gg_free": (None, [ctypes.c_void_p]),
@@ -315,6 +320,43 @@ class Plan:
 
     def sync(self):
         _check(lib().gg_sync(self._h), self._h)
+
+    # ------------------------------------------------------- adjoint form
+    def _ptrs3(self, ts):
+        return _VP3(*[None if t is None else _dev_ptr(t, self.dtype, self._cells()) for t in ts])
+
+    def zeldovich_adjoint(self, g_psi, out=None):
+        """sum_j J_j^T g_psi[j] (J_j: noise -> psi_j); entries may be None."""
+        out = self.empty() if out is None else out
+        self._bind_stream()
+        _check(lib().gg_zeldovich_adjoint(self._h, self._ptrs3(g_psi),
+                                          _dev_ptr(out, self.dtype, self._cells())), self._h)
+        return out
+
+    def smooth(self, field, radius, out=None):
+        """Gaussian smoothing exp(-k^2 R^2/2) (symmetric; its own adjoint)."""
+        out = self.empty() if out is None else out
+        self._bind_stream()
+        _check(lib().gg_smooth(self._h, float(radius), _dev_ptr(field, self.dtype, self._cells()),
+                               _dev_ptr(out, self.dtype, self._cells())), self._h)
+        return out
+
+    def cic_density(self, psi, out=None):
+        """CIC density contrast of the particles at q + psi."""
+        out = self.empty() if out is None else out
+        self._bind_stream()
+        _check(lib().gg_cic_density(self._h, self._ptrs3(psi),
+                                    _dev_ptr(out, self.dtype, self._cells())), self._h)
+        return out
+
+    def cic_density_adjoint(self, psi, g_delta):
+        """Transpose of the CIC Jacobian at psi applied to g_delta: 3 grids."""
+        out = [self.empty() for _ in range(3)]
+        self._bind_stream()
+        _check(lib().gg_cic_density_adjoint(self._h, self._ptrs3(psi),
+                                            _dev_ptr(g_delta, self.dtype, self._cells()),
+                                            self._ptrs3(out)), self._h)
+        return out
 
     def autotune(self, reps=3):
         """Time each tile variant of the transform passes; keep the fastest per pass."""

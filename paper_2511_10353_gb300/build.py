@@ -30,6 +30,7 @@ SOURCES = [
     "gg_kernels_f64.cu",
     "gg_kernels_common.cu",
     "gg_static.cu",
+    "gg_cic.cu",
     "gg_api.cpp",
     "gg_cosmo.cpp",
 ]

@@ -38,6 +38,8 @@ struct Tables {
   void *tw_half = nullptr;  // length N/2
   void *s_delta = nullptr;  // S(m2) N^-3/2, 3 (N/2)^2 + 1 entries (density filter, Eq. 1)
   void *u_phi = nullptr;    // S(m2) N^-3/2 (L / 2 pi) / m2 (potential; psi~_j = i m_j U W~)
+  void *smooth = nullptr;   // exp(-k^2 R^2 / 2) / N^3 for the last gg_smooth radius
+  double smooth_radius = -1.0;
 };
 
 }  // namespace
@@ -284,7 +286,8 @@ void release(gg_plan_t *plan) {
   if (!plan) return;
   void *bufs[] = {plan->work,        plan->work2,         plan->work3,
                   plan->tab.tw_n,    plan->tab.tw_half,   plan->tab.s_delta,
-                  plan->tab.u_phi,   plan->err,           plan->noise_stage};
+                  plan->tab.u_phi,   plan->err,           plan->noise_stage,
+                  plan->tab.smooth};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (auto &slot : plan->stage)
@@ -417,7 +420,7 @@ gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
 
 template <typename R>
 gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void *pos, void *vel,
-                    bool mul_kz) {
+                    bool mul_kz, bool accumulate = false, double alpha = 1.0) {
   const int n = (int)plan->p.n;
   gg::ZInvArgs z{};
   z.src = src;
@@ -429,6 +432,8 @@ gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void 
   z.lines_per_cta = plan->z_lines;
   z.comp = comp;
   z.mul_kz = mul_kz ? 1 : 0;
+  z.accumulate = accumulate ? 1 : 0;
+  z.alpha = alpha;
   z.box = plan->p.box;
   z.cell = plan->p.box / (double)n;
   z.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
@@ -546,14 +551,15 @@ gg_status run_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise, void 
 }
 
 template <typename R>
-gg_status run_density(gg_plan_t *plan, uint64_t seed, const void *noise, void *delta) {
+gg_status run_density(gg_plan_t *plan, uint64_t seed, const void *noise, void *delta,
+                      const void *table = nullptr) {
   gg_status st = forward_zy<R>(plan, seed, noise);
   if (st != GG_OK) return st;
   gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
   x.fwd = 1;
   x.inv = 1;
   x.pre = 1;
-  x.table = plan->tab.s_delta;
+  x.table = table ? table : plan->tab.s_delta;
   x.nout = 1;
   x.dst[0] = plan->work;
   x.mul[0] = gg::kMulNone;
@@ -712,6 +718,57 @@ gg_status autotune(gg_plan_t *plan, int reps) {
   cudaFree(tmp);
   for (int i = 0; i < 6; ++i) plan->variant[i] = best_v[i];
   return st;
+}
+
+// ------------------------------------------------------------ adjoint form
+// psi_j = J_j W with J_j = F^-1 diag(i m_j U) F (F the unnormalised DFT,
+// U real and even in k). i m_j U is purely imaginary and Hermitian, so
+// J_j^T = -J_j and dL/dW = sum_j J_j^T g_j = -sum_j J_j g_j: the forward
+// chain run once per component on g_j, accumulated with weight -1. No
+// transform intermediates are stored.
+template <typename R>
+gg_status run_adjoint(gg_plan_t *plan, const void *const g_psi[3], void *g_noise) {
+  cudaError_t e = cudaMemsetAsync(g_noise, 0, (size_t)plan->cells * sizeof(R), plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemsetAsync");
+  for (int j = 0; j < 3; ++j) {
+    if (!g_psi || !g_psi[j]) continue;
+    const bool want[3] = {j == 0, j == 1, j == 2};
+    void *src[3];
+    gg_status st = spectral_passes<R>(plan, 0, g_psi[j], want, nullptr, src);
+    if (st != GG_OK) return st;
+    st = zinv_pass<R>(plan, j, src[j], g_noise, nullptr, nullptr, j == 2, true, -1.0);
+    if (st != GG_OK) return st;
+  }
+  return GG_OK;
+}
+
+template <typename R>
+gg_status run_smooth(gg_plan_t *plan, double radius, const void *in, void *out) {
+  const int64_t n = plan->p.n;
+  if (radius != plan->tab.smooth_radius) {
+    const size_t cnt = table_entries(n);
+    std::vector<R> t(cnt);
+    const double kf = 2.0 * kPi / plan->p.box;
+    const double n3 = (double)n * n * n;
+    for (size_t i = 0; i < cnt; ++i) t[i] = (R)(std::exp(-0.5 * kf * kf * (double)i * radius * radius) / n3);
+    cudaError_t e;
+    if (!plan->tab.smooth && (e = cudaMalloc(&plan->tab.smooth, cnt * sizeof(R))) != cudaSuccess)
+      return fail(plan, GG_ENOMEM, "cudaMalloc of the smoothing table failed");
+    if ((e = cudaMemcpy(plan->tab.smooth, t.data(), cnt * sizeof(R), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return cuda_fail(plan, e, "smoothing table upload");
+    plan->tab.smooth_radius = radius;
+  }
+  return run_density<R>(plan, 0, in, out, plan->tab.smooth);
+}
+
+gg::CicArgs cic_args(const gg_plan_t *plan, const void *const psi[3]) {
+  gg::CicArgs a{};
+  for (int j = 0; j < 3; ++j) a.psi[j] = psi[j];
+  a.n = (int)plan->p.n;
+  a.cell = plan->p.box / (double)plan->p.n;
+  a.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
+  return a;
 }
 
 // ------------------------------------------------------------ batched form
@@ -1032,6 +1089,49 @@ gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
   }
   return plan->real_bytes == 8 ? run_zeldovich<double>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev)
                                : run_zeldovich<float>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev);
+}
+
+gg_status gg_zeldovich_adjoint(gg_plan_t *plan, const void *const g_psi_dev[3], void *g_noise_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!g_noise_dev || !aligned16(g_noise_dev)) return fail(plan, GG_EINVAL, "g_noise_dev NULL or unaligned");
+  for (int j = 0; j < 3; ++j)
+    if (g_psi_dev && g_psi_dev[j] && !aligned16(g_psi_dev[j]))
+      return fail(plan, GG_EINVAL, "g_psi buffer unaligned");
+  return plan->real_bytes == 8 ? run_adjoint<double>(plan, g_psi_dev, g_noise_dev)
+                               : run_adjoint<float>(plan, g_psi_dev, g_noise_dev);
+}
+
+gg_status gg_smooth(gg_plan_t *plan, double radius, const void *in_dev, void *out_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!(radius >= 0) || !std::isfinite(radius)) return fail(plan, GG_EINVAL, "radius must be >= 0");
+  if (!in_dev || !out_dev || !aligned16(in_dev) || !aligned16(out_dev))
+    return fail(plan, GG_EINVAL, "in/out NULL or unaligned");
+  return plan->real_bytes == 8 ? run_smooth<double>(plan, radius, in_dev, out_dev)
+                               : run_smooth<float>(plan, radius, in_dev, out_dev);
+}
+
+gg_status gg_cic_density(gg_plan_t *plan, const void *const psi_dev[3], void *delta_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!psi_dev || !psi_dev[0] || !psi_dev[1] || !psi_dev[2] || !delta_dev)
+    return fail(plan, GG_EINVAL, "psi_dev[3] and delta_dev are required");
+  gg::CicArgs a = cic_args(plan, psi_dev);
+  a.delta = delta_dev;
+  const cudaError_t e = plan->real_bytes == 8 ? gg::launch_cic_deposit<double>(a, plan->stream)
+                                              : gg::launch_cic_deposit<float>(a, plan->stream);
+  return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, "CIC deposit");
+}
+
+gg_status gg_cic_density_adjoint(gg_plan_t *plan, const void *const psi_dev[3], const void *g_delta_dev,
+                                 void *const g_psi_dev[3]) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!psi_dev || !psi_dev[0] || !psi_dev[1] || !psi_dev[2] || !g_delta_dev || !g_psi_dev)
+    return fail(plan, GG_EINVAL, "psi_dev[3], g_delta_dev and g_psi_dev are required");
+  gg::CicArgs a = cic_args(plan, psi_dev);
+  a.g_delta = g_delta_dev;
+  for (int j = 0; j < 3; ++j) a.g_psi[j] = g_psi_dev[j];
+  const cudaError_t e = plan->real_bytes == 8 ? gg::launch_cic_adjoint<double>(a, plan->stream)
+                                              : gg::launch_cic_adjoint<float>(a, plan->stream);
+  return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, "CIC adjoint");
 }
 
 gg_status gg_zeldovich_host(gg_plan_t *plan, uint64_t seed, const void *noise_host,

@@ -254,7 +254,14 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(co
       for (int r = 0; r < RL; ++r) {
         const int n = p + P * b + r * SPANL;
         const C z = v[b * RL + r];
-        if (psi) psi[n] = z;
+        if (psi) {
+          if (a.accumulate) {
+            const C o = psi[n];
+            psi[n] = C{o.x + (R)a.alpha * z.x, o.y + (R)a.alpha * z.y};
+          } else {
+            psi[n] = z;
+          }
+        }
         if (pos) {
           R q0 = qline, q1 = qline;
           if (a.comp == 2) {

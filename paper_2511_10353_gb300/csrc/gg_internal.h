@@ -111,10 +111,28 @@ struct ZInvArgs {
   int *err;               // device error word
   int variant;            // tile variant of the size-specialised kernel
   int64_t lines_per_real; // lines of one realization (<= 0: nlines)
+  int accumulate;         // psi output: psi += alpha * result instead of psi = result
+  double alpha;
   void *const *psi_list;  // batched form: device arrays of per-realization outputs
   void *const *pos_list;  // (entries may be null); when set they replace psi/pos/vel
   void *const *vel_list;
 };
+
+// Cloud-in-cell density of the Zel'dovich particles and its adjoint. Particle
+// p sits at u_j = i_j + q_offset - 1/2 + psi_j[p] / cell (grid units, nodes at
+// cell centres); it adds prod_j w_j to the 8 nodes around it with linear
+// weights (1 - f, f), periodic.
+struct CicArgs {
+  const void *psi[3];     // N^3 reals each
+  void *delta;            // deposit: N^3 reals (set to -1 first, then += weights)
+  const void *g_delta;    // adjoint: N^3 reals
+  void *g_psi[3];         // adjoint: d/dpsi_j of sum_c g(c) delta(c)
+  int n;
+  double cell;            // L / N
+  double q_offset;        // 0.5 or 0
+};
+template <typename R> cudaError_t launch_cic_deposit(const CicArgs &a, cudaStream_t s);
+template <typename R> cudaError_t launch_cic_adjoint(const CicArgs &a, cudaStream_t s);
 
 struct NoiseArgs {
   void *out;              // N^3 reals

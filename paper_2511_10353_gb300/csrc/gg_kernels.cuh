@@ -361,7 +361,14 @@ __global__ void k_zinv(const ZInvArgs a) {
   for (int i = 0; i < E; ++i) {
     const int n = p + P * i;
     const C v = buf[lay(l, n)];
-    if (psi) psi[n] = v;
+    if (psi) {
+      if (a.accumulate) {
+        const C o = psi[n];
+        psi[n] = C{o.x + (R)a.alpha * v.x, o.y + (R)a.alpha * v.y};
+      } else {
+        psi[n] = v;
+      }
+    }
     if (pos) {
       R q0 = qline, q1 = qline;
       if (a.comp == 2) {
