@@ -40,6 +40,9 @@ struct Tables {
   void *u_phi = nullptr;    // S(m2) N^-3/2 (L / 2 pi) / m2 (potential; psi~_j = i m_j U W~)
   void *smooth = nullptr;   // exp(-k^2 R^2 / 2) / N^3 for the last gg_smooth radius
   double smooth_radius = -1.0;
+  // FP32 shared-memory forms of the three filters (see AxisArgs::interp)
+  void *interp_u = nullptr, *interp_s = nullptr, *interp_smooth = nullptr;
+  int interp_cells = 0;
 };
 
 }  // namespace
@@ -229,6 +232,33 @@ void filter_values(const gg_params *p, const gg::cosmo::Model &m, double growth,
   }
 }
 
+// Shared-memory form of a filter F(m2) (FP32 size-specialised kernels): the
+// exact values for m2 < kInterpExact, then for each unit cell [j, j+1) of
+// m = sqrt(m2) the FP64 values and derivatives (F_j, F'_j, F_j+1, F'_j+1) of
+// F as a function of continuous m, rounded once; cubic Hermite interpolation
+// inside a cell is accurate to < 1e-6 relative for m >= 32.
+template <class F>
+gg_status upload_interp(gg_plan_t *plan, void **dst, const F &fm) {
+  const int64_t n = plan->p.n;
+  const int cells = (int)std::ceil(std::sqrt(3.0) * (double)(n / 2)) + 2;
+  std::vector<float> buf(gg::kInterpExact + 4 * (size_t)cells);
+  for (int q = 0; q < gg::kInterpExact; ++q) buf[q] = (float)fm(std::sqrt((double)q), q);
+  auto d = [&](double x) {
+    const double h = 1e-4 * std::max(1.0, x);
+    return (fm(x + h, -1) - fm(x - h, -1)) / (2 * h);
+  };
+  for (int j = 0; j < cells; ++j) {
+    const double x0 = std::max((double)j, 1.0), x1 = (double)j + 1.0;  // cells below 32 are unused
+    float *c = buf.data() + gg::kInterpExact + 4 * (size_t)j;
+    c[0] = (float)fm(x0, -1);
+    c[1] = (float)d(x0);
+    c[2] = (float)fm(x1, -1);
+    c[3] = (float)d(x1);
+  }
+  plan->tab.interp_cells = cells;
+  return upload(plan, dst, buf);
+}
+
 template <typename R>
 gg_status build_tables(gg_plan_t *plan, const gg::cosmo::Model &m) {
   const int64_t n = plan->p.n;
@@ -245,7 +275,22 @@ gg_status build_tables(gg_plan_t *plan, const gg::cosmo::Model &m) {
     up[i] = i ? (R)(s[i] * norm * plan->p.box / (2.0 * kPi * (double)i)) : (R)0;
   }
   if ((st = upload(plan, &plan->tab.s_delta, sd)) != GG_OK) return st;
-  return upload(plan, &plan->tab.u_phi, up);
+  if ((st = upload(plan, &plan->tab.u_phi, up)) != GG_OK) return st;
+  if (sizeof(R) == 4 && plan->p.cosmo.tf != GG_TF_TABLE) {
+    // smooth analytic spectra: FP32 kernels interpolate instead of gathering
+    const double box = plan->p.box, vol = box * box * box, growth = plan->info.growth;
+    auto s_of = [&](double mm, int q) {  // S(m) N^-3/2 at continuous m (q: integer m2 or -1)
+      if (q == 0 || mm <= 0) return 0.0;
+      return growth * std::sqrt(m.power(2.0 * kPi * mm / box) / vol) * norm;
+    };
+    auto u_of = [&](double mm, int q) {
+      if (q == 0 || mm <= 0) return 0.0;
+      return s_of(mm, q) * box / (2.0 * kPi * mm * mm);
+    };
+    if ((st = upload_interp(plan, &plan->tab.interp_s, s_of)) != GG_OK) return st;
+    if ((st = upload_interp(plan, &plan->tab.interp_u, u_of)) != GG_OK) return st;
+  }
+  return GG_OK;
 }
 
 template <typename R>
@@ -287,7 +332,8 @@ void release(gg_plan_t *plan) {
   void *bufs[] = {plan->work,        plan->work2,         plan->work3,
                   plan->tab.tw_n,    plan->tab.tw_half,   plan->tab.s_delta,
                   plan->tab.u_phi,   plan->err,           plan->noise_stage,
-                  plan->tab.smooth};
+                  plan->tab.smooth,  plan->tab.interp_u,  plan->tab.interp_s,
+                  plan->tab.interp_smooth};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (auto &slot : plan->stage)
@@ -489,6 +535,8 @@ gg_status spectral_passes(gg_plan_t *plan, uint64_t seed, const void *noise, con
   x.inv = 1;
   x.pre = 1;
   x.table = plan->tab.u_phi;
+  x.interp = plan->tab.interp_u;
+  x.interp_cells = plan->tab.interp_cells;
   x.nout = 0;
   if (want[0]) {
     x.dst[x.nout] = plan->work;
@@ -552,7 +600,7 @@ gg_status run_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise, void 
 
 template <typename R>
 gg_status run_density(gg_plan_t *plan, uint64_t seed, const void *noise, void *delta,
-                      const void *table = nullptr) {
+                      const void *table = nullptr, const void *interp = nullptr) {
   gg_status st = forward_zy<R>(plan, seed, noise);
   if (st != GG_OK) return st;
   gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
@@ -560,6 +608,8 @@ gg_status run_density(gg_plan_t *plan, uint64_t seed, const void *noise, void *d
   x.inv = 1;
   x.pre = 1;
   x.table = table ? table : plan->tab.s_delta;
+  x.interp = interp ? interp : (table ? nullptr : plan->tab.interp_s);
+  x.interp_cells = plan->tab.interp_cells;
   x.nout = 1;
   x.dst[0] = plan->work;
   x.mul[0] = gg::kMulNone;
@@ -758,8 +808,17 @@ gg_status run_smooth(gg_plan_t *plan, double radius, const void *in, void *out) 
         cudaSuccess)
       return cuda_fail(plan, e, "smoothing table upload");
     plan->tab.smooth_radius = radius;
+    if (sizeof(R) == 4) {
+      auto g_of = [&](double mm, int) { return std::exp(-0.5 * kf * kf * mm * mm * radius * radius) / n3; };
+      if (plan->tab.interp_smooth) {
+        cudaFree(plan->tab.interp_smooth);
+        plan->tab.interp_smooth = nullptr;
+      }
+      gg_status st = upload_interp(plan, &plan->tab.interp_smooth, g_of);
+      if (st != GG_OK) return st;
+    }
   }
-  return run_density<R>(plan, 0, in, out, plan->tab.smooth);
+  return run_density<R>(plan, 0, in, out, plan->tab.smooth, plan->tab.interp_smooth);
 }
 
 gg::CicArgs cic_args(const gg_plan_t *plan, const void *const psi[3]) {
@@ -836,6 +895,8 @@ gg_status group_passes(gg_batch::Group &g, cudaStream_t s, uint32_t sig) {
     x.inv = 1;
     x.pre = 1;
     x.table = plan->tab.u_phi;
+    x.interp = plan->tab.interp_u;
+    x.interp_cells = plan->tab.interp_cells;
     x.nout = 2;
     x.dst[0] = g.work[0];
     x.mul[0] = gg::kMulIm;

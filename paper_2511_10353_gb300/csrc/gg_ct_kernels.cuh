@@ -31,11 +31,21 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
+  // interpolated filter (FP32): exact values, then Hermite cells, after the tiles
+  float *f_exact = reinterpret_cast<float *>(bufs + 2 * TILE_STRIDE);
+  float4 *f_cells = reinterpret_cast<float4 *>(f_exact + kInterpExact);
   const int tid = threadIdx.x;
   const int64_t per_real = (int64_t)N * INNER;
   const int64_t ntiles = per_real * (a.nbatch > 0 ? a.nbatch : 1);
   const C *tw = reinterpret_cast<const C *>(a.tw);
   const R *table = reinterpret_cast<const R *>(a.table);
+  const bool interp = sizeof(R) == 4 && a.pre && a.interp;
+  if (interp) {
+    const float *src = reinterpret_cast<const float *>(a.interp);
+    for (int i = tid; i < kInterpExact; i += blockDim.x) f_exact[i] = src[i];
+    const float4 *cs = reinterpret_cast<const float4 *>(src + kInterpExact);
+    for (int i = tid; i < a.interp_cells; i += blockDim.x) f_cells[i] = cs[i];
+  }
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -79,7 +89,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
       const int m = ct_freq(n, N);
       return (n == HALF || nyq_outer) ? -1 : m * m + m_outer * m_outer + kz * kz;
     };
-    if (a.pre) {
+    if (a.pre && !interp) {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -111,7 +121,23 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
           const int q = tab_index(p + P * b + r * SPAN);
-          const R f = q >= 0 ? __ldg(table + q) : (R)0;
+          R f;
+          if (q < 0) {
+            f = (R)0;
+          } else if (!interp) {
+            f = __ldg(table + q);
+          } else if (q < kInterpExact) {
+            f = (R)f_exact[q];
+          } else {  // cubic Hermite in m = sqrt(m2), unit cells
+            const float mf = (float)q;
+            const float m = mf * rsqrtf(mf);
+            const int j = (int)m;
+            const float t = m - (float)j;
+            const float4 cc = f_cells[j];
+            const float t2 = t * t, t3 = t2 * t;
+            f = (R)((2.f * t3 - 3.f * t2 + 1.f) * cc.x + (t3 - 2.f * t2 + t) * cc.y +
+                    (3.f * t2 - 2.f * t3) * cc.z + (t3 - t2) * cc.w);
+          }
           V[b * RH + r] = C{f * V[b * RH + r].x, f * V[b * RH + r].y};
         }
     }
@@ -345,7 +371,9 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   cudaError_t e = make_map<R>(&map, a);
   if (e != cudaSuccess) return e;
   const size_t tile = ((size_t)N * Pol::B * 2 * sizeof(R) + 127) & ~(size_t)127;
-  const size_t smem = 128 + 2 * tile;
+  const bool interp = sizeof(R) == 4 && a.pre && a.interp;
+  const size_t smem = 128 + 2 * tile +
+                      (interp ? kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16 : 0);
   auto kern = k_axis_ct<R, N, V>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);

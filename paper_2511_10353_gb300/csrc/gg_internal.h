@@ -10,6 +10,7 @@
 namespace gg {
 
 constexpr int kMaxStages = 16;
+constexpr int kInterpExact = 1024;  // m2 below this: exact table values in shared memory
 
 // Radix schedule of one complex transform of length `len` done inside a CTA
 // (Stockham autosort, decimation in time). Stage s combines radix[s] partial
@@ -64,6 +65,12 @@ struct AxisArgs {
   const void *tw;         // exp(-2 pi i t / N)
   int pre;                // 1: multiply the handed-off spectrum by table[m2]
   const void *table;      // T(m2)
+  // FP32 size-specialised kernels: T from shared memory instead of a gather
+  // from the global table: exact values for m2 < kInterpExact, above that a
+  // cubic Hermite interpolation in m = sqrt(m2) over unit cells (float4:
+  // F_j, F'_j, F_j+1, F'_j+1). nullptr: gather from `table`.
+  const void *interp;
+  int interp_cells;
   int e;                  // elements per thread (multiple of every radix)
   int rows_box;           // TMA box height (divisor of N, <= 256); 0: plain loads
   int *err;               // device error word
