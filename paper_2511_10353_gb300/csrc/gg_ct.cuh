@@ -177,7 +177,8 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
 // Strided pass, variant
 //   0: E = lcm of the radices, rows of up to 128 bytes, <= 512 threads
 //   1: E doubled (two butterflies per thread and stage), rows of up to 128 bytes
-//   2: E doubled, rows halved (a smaller CTA; several CTAs share an SM)
+//   2: E doubled where it fits, rows halved (a smaller CTA: several share an
+//      SM, or two outputs fit the register budget)
 // Whether the handed-off spectrum of two outputs may stay in registers is
 // estimated from the register budget; otherwise one output per launch.
 template <typename R, int N, int V> struct AxisPolicy {
@@ -189,7 +190,7 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int pick() {
     int b = 128 / CB;
     while (b > 1 && ((N / 2) % b != 0 || P * b > 512 || 2 * (N * b * CB) > 200 * 1024)) b /= 2;
-    if (V == 2 && DOUBLE_OK && b * CB > 32) b /= 2;
+    if (V == 2 && b * CB > 32) b /= 2;
     return b;
   }
   static constexpr int B = pick();
@@ -200,8 +201,8 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
 };
 
-// z passes: lines per tile, variant 0 ~256 threads (two dense tiles + one
-// padded tile within 160 KB), variant 1 half as many lines.
+// z passes: lines per tile, variant 0 ~256 threads (sized so that two dense
+// tiles and a padded tile fit in 160 KB), variant 1 half as many lines.
 template <typename R, int N, int V> struct ZPolicy {
   static constexpr int M = N / 2;
   static constexpr int E = elems(M);
@@ -218,6 +219,17 @@ template <typename R, int N, int V> struct ZPolicy {
   static constexpr int THREADS = P * L;
   static constexpr int DENSE = L * M;        // complex values of one dense tile
   static constexpr int WORK = L * LD;        // complex values of the padded tile
+  // CTAs per SM the register allocation must leave room for: enough for 16
+  // warps, as far as the shared memory of the pass allows (inverse: a dense
+  // staging tile and the padded tile; forward: the padded tile). FP64 lines
+  // need twice the registers and run at the FP64 rate: no bound there.
+  static constexpr int min_blocks(int smem) {
+    const int by_smem = (228 * 1024) / smem, by_warps = 512 / THREADS;
+    const int m = by_smem < by_warps ? by_smem : by_warps;
+    return sizeof(R) == 4 && m > 0 ? m : 1;
+  }
+  static constexpr int MINB_INV = min_blocks(128 + DENSE * CB + WORK * CB);
+  static constexpr int MINB_FWD = min_blocks(WORK * CB);
 };
 
 }  // namespace ct

@@ -105,15 +105,15 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
     }
     auto ld_smem = [&](int n) { return buf[n * B + c]; };
     auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
-    C V[E];
+    C X[E];
     if (a.fwd) {
       ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
-      ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, V);
+      ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, X);
     } else {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int r = 0; r < RH; ++r) V[b * RH + r] = buf[(p + P * b + r * SPAN) * B + c];
+        for (int r = 0; r < RH; ++r) X[b * RH + r] = buf[(p + P * b + r * SPAN) * B + c];
     }
     if (a.pre) {
 #pragma unroll
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
             f = (R)((2.f * t3 - 3.f * t2 + 1.f) * cc.x + (t3 - 2.f * t2 + t) * cc.y +
                     (3.f * t2 - 2.f * t3) * cc.z + (t3 - t2) * cc.w);
           }
-          V[b * RH + r] = C{f * V[b * RH + r].x, f * V[b * RH + r].y};
+          X[b * RH + r] = C{f * X[b * RH + r].x, f * X[b * RH + r].y};
         }
     }
     if (!a.inv) {  // forward only: the spectrum to dst[0]
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * a.stride] = V[b * RH + r];
+        for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * a.stride] = X[b * RH + r];
       __syncthreads();
       continue;
     }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
           const int n = p + P * b + r * SPAN;
-          const C v = V[b * RH + r];
+          const C v = X[b * RH + r];
           const R f = n == HALF ? (R)0 : (R)ct_freq(n, N);
           W[b * RH + r] = im ? C{-f * v.y, f * v.x} : v;
         }
@@ -194,12 +194,14 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
 template <int LD> __device__ __forceinline__ int zpad(int l, int n) { return l * LD + n + (n >> 4); }
 
 // Inverse z pass (c2r) + Eq. 3 epilogue, persistent: one thread bulk-copies
-// the next block of L contiguous half-spectrum lines into a dense shared
-// buffer while the CTA works on the current one. The c2r pre-processing reads
-// the dense buffer and writes the padded work tile; the transform runs there;
-// the last stage's outputs (natural order) feed the epilogue from registers.
+// a block of L contiguous half-spectrum lines into a dense shared buffer. The
+// c2r pre-processing moves it into the padded work tile, after which the
+// buffer is free and the copy of the CTA's next block starts; it lands while
+// the transform and the epilogue of the current block run. The last stage's
+// outputs (natural order) feed the epilogue from registers.
 template <typename R, int N, int V>
-__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(const ZInvArgs a) {
+__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_INV)
+    k_zinv_ct(const ZInvArgs a) {
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
@@ -207,42 +209,33 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(co
   constexpr int RL = ct::radix_of(M, S - 1, true), SPANL = M / RL, NBL = E / RL;
   constexpr int DENSE_STRIDE = (int)(((Pol::DENSE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   C *dense = reinterpret_cast<C *>(smem_raw + 128);
-  C *work = dense + 2 * DENSE_STRIDE;
+  C *work = dense + DENSE_STRIDE;
   const int tid = threadIdx.x;
   const int64_t ntiles = a.nlines / L;
   const C *tw_half = reinterpret_cast<const C *>(a.tw_half);
   const C *twf = reinterpret_cast<const C *>(a.tw_full);
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int64_t t, int sb) {
-    mbar_arrive_expect_tx(&bars[sb], (uint32_t)(Pol::DENSE * sizeof(C)));
-    bulk_load(dense + sb * DENSE_STRIDE, reinterpret_cast<const C *>(a.src) + t * Pol::DENSE,
-              (uint32_t)(Pol::DENSE * sizeof(C)), &bars[sb]);
+  auto issue = [&](int64_t t) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(Pol::DENSE * sizeof(C)));
+    bulk_load(dense, reinterpret_cast<const C *>(a.src) + t * Pol::DENSE,
+              (uint32_t)(Pol::DENSE * sizeof(C)), bar);
   };
   const R box = (R)a.box, cell = (R)a.cell, qo = (R)a.q_offset, vfac = (R)a.vfac;
   int64_t t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
+  if (tid == 0 && t < ntiles) issue(t);
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-    const int sb = it & 1;
     const int64_t tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) {
-      fence_proxy_async_smem();
-      issue(tn, sb ^ 1);
-    }
     int l = tid / P, p = tid - (tid / P) * P;
     asm volatile("" : "+r"(l), "+r"(p));
-    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err));
-    if (!ok) {
-      if (tid == 0 && tn < ntiles) mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
-      return;
-    }
-    const C *dl = dense + sb * DENSE_STRIDE + l * M;
+    const bool ok = __syncthreads_and(mbar_wait(bar, (uint32_t)(it & 1), a.err));
+    if (!ok) return;  // nothing else in flight: the next copy is issued after this wait
+    const C *dl = dense + l * M;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k = p + P * i;
@@ -257,6 +250,10 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(co
       work[zpad<LD>(l, k)] = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
     }
     __syncthreads();
+    if (tid == 0 && tn < ntiles) {  // the dense buffer has been read: fetch the next block
+      fence_proxy_async_smem();
+      issue(tn);
+    }
     auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
     auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
     ct::stages<R, M, E, true, 0, S - 1>(p, tw_half, ld_w, st_w);
@@ -306,7 +303,8 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zinv_ct(co
 // work tile, the length-N/2 transform in place, then the real-input unpacking
 // X_k = (Z_k + conj Z_{M-k})/2 - i/2 e^{-2 pi i k/N} (Z_k - conj Z_{M-k}).
 template <typename R, int N, int V>
-__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, 1) k_zfwd_ct(const ZFwdArgs a) {
+__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_FWD)
+    k_zfwd_ct(const ZFwdArgs a) {
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
@@ -385,7 +383,7 @@ template <typename R, int N, int V>
 cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
   using Pol = ct::ZPolicy<R, N, V>;
   const size_t dense = (Pol::DENSE * 2 * sizeof(R) + 127) & ~(size_t)127;
-  const size_t smem = 128 + 2 * dense + (size_t)Pol::WORK * 2 * sizeof(R);
+  const size_t smem = 128 + dense + (size_t)Pol::WORK * 2 * sizeof(R);
   auto kern = k_zinv_ct<R, N, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;

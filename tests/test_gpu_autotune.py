@@ -28,7 +28,8 @@ def gg():
     return m
 
 
-@pytest.mark.parametrize("n,prec", [(64, "f32"), (128, "f32"), (192, "f32"), (512, "f32"), (64, "f64")])
+@pytest.mark.parametrize("n,prec", [(64, "f32"), (128, "f32"), (192, "f32"), (384, "f32"), (512, "f32"),
+                                    (64, "f64")])
 def test_variants_bit_identical(gg, n, prec):
     plan = gg.Plan(n, float(n), BBKS, 50.0, prec)
     ref = None
