@@ -302,6 +302,49 @@ gg_status gg_cic_density(gg_plan_t *plan, const void *const psi_dev[3], void *de
 gg_status gg_cic_density_adjoint(gg_plan_t *plan, const void *const psi_dev[3],
                                  const void *g_delta_dev, void *const g_psi_dev[3]);
 
+/* ---------------------------------------------------------------- refinement
+ * Appendix A: a white-noise field of higher resolution whose large scales are
+ * those of a given parent field. Each patch of N_L parent cells per axis is
+ * expanded over an orthonormal parent basis F (Eq. A.1); the N_L^3
+ * coefficients are kept, N_H^3 - N_L^3 new unit Gaussian coefficients are
+ * added, and the patch's N_H^3 child values are W = sum a_ijk E_i E_j E_k
+ * (Eqs. A.14, A.28). Kinds (cells per axis N_L -> N_H, bases): */
+typedef enum {
+  GG_REFINE_HR = 0,        /* 1 -> 2, Eqs. A.2-A.4 (Hoffman-Ribak) */
+  GG_REFINE_3_2 = 1,       /* 2 -> 3, F: Eqs. A.5-A.6, E: Eqs. A.7-A.9 */
+  GG_REFINE_2 = 2,         /* 2 -> 4, F: Eqs. A.5-A.6, E: Eqs. A.10-A.13 */
+  GG_REFINE_2_LINEAR = 3,  /* 2 -> 4, E: Eqs. A.20-A.23 */
+  GG_REFINE_2_SINE = 4,    /* 2 -> 4, E: Eqs. A.24-A.27 */
+  GG_REFINE_4_3 = 5        /* 3 -> 4, F: the three-cell basis of Eqs. A.7-A.9,
+                              E: Eqs. A.10-A.13 */
+} gg_refine_kind;
+
+typedef struct {
+  int64_t n;               /* parent grid points per axis (periodic), a multiple of N_L */
+  gg_prec prec;
+  gg_refine_kind kind;
+  int64_t origin[3];       /* first parent cell of the refined box, multiples of N_L, in [0, n) */
+  int64_t extent[3];       /* parent cells per axis to refine, multiples of N_L, <= n;
+                              0 => n (with origin 0: the whole box) */
+} gg_refine_params;
+
+/* Shape of the child grid gg_refine_noise writes: extent * N_H / N_L per axis. */
+gg_status gg_refine_dims(const gg_refine_params *p, int64_t dims[3]);
+
+/* Refine the parent white noise parent_dev (n^3 reals, [x][y][z], z fastest)
+ * over the box of *p into child_dev (dims[0] x dims[1] x dims[2] reals of the
+ * same type, [x][y][z]); both caller-owned, 16-byte aligned device memory.
+ * The new coefficient (i, j, k) of the patch whose first child cell is
+ * (X, Y, Z) is the white noise of seed_child (the Philox / Box-Muller mapping
+ * of gg_white_noise) at child cell (X+i, Y+j, Z+k) of the whole refined grid
+ * of n N_H / N_L cells per axis: the result is independent of the launch
+ * shape, and a refined sub-box equals that part of the refined whole box.
+ * Parent indices wrap periodically. Asynchronous on `stream` (a
+ * cudaStream_t, NULL = legacy default stream). Invalid arguments return
+ * GG_EINVAL before any device work, with a message in gg_last_error(NULL). */
+gg_status gg_refine_noise(const gg_refine_params *p, const void *parent_dev, uint64_t seed_child,
+                          void *child_dev, void *stream);
+
 /* Wait for the plan's stream; return the first latched device error, if any. */
 gg_status gg_sync(gg_plan_t *plan);
 

@@ -111,34 +111,57 @@ def child_size(n, kind):
     return n // nl * nh
 
 
+def refine_patches(v, kind, seed_child, n, gp):
+    """Child values of a list of patches (Eqs. A.14, A.28).
+
+    ``v``: (P, N_L, N_L, N_L) parent values of each patch; ``gp``: (P, 3)
+    patch coordinates in the whole grid (patch (X, Y, Z) holds parent cells
+    N_L X .. N_L X + N_L - 1 per axis); ``n``: parent points per axis.
+    Returns (P, N_H, N_H, N_H)."""
+    nl, nh, f, e = KINDS[kind]
+    nc = child_size(n, kind)
+    v = np.asarray(v, dtype=np.float64).reshape(-1, nl, nl, nl)
+    gp = np.asarray(gp, dtype=np.int64).reshape(-1, 3)
+    # every coefficient position takes the child noise at its child cell ...
+    k = np.arange(nh)
+    cx = gp[:, 0, None] * nh + k  # (P, N_H) child coordinates per axis
+    cy = gp[:, 1, None] * nh + k
+    cz = gp[:, 2, None] * nh + k
+    idx = (cx[:, :, None, None] * nc + cy[:, None, :, None]) * nc + cz[:, None, None, :]
+    a = noise_at(seed_child, idx.ravel()).reshape(-1, nh, nh, nh)
+    # ... except the first N_L^3: a_ijk = sum_mnl F_i(m) F_j(n) F_k(l) V(m, n, l)
+    a[:, :nl, :nl, :nl] = np.einsum("im,jn,kl,pmnl->pijk", f, f, f, v)
+    # W(m, n, l) = sum_ijk a_ijk E_i(m) E_j(n) E_k(l)
+    return np.einsum("im,jn,kl,pijk->pmnl", e, e, e, a)
+
+
 def refine(parent, kind, seed_child, origin=(0, 0, 0), extent=None):
     """Refined white noise of the sub-box [origin, origin + extent) (parent
     cells, periodic) of the parent grid; returns the child grid of
-    extent * N_H / N_L cells per axis (Eqs. A.14, A.28)."""
+    extent * N_H / N_L cells per axis."""
     parent = np.asarray(parent, dtype=np.float64)
     n = parent.shape[0]
-    nl, nh, f, e = KINDS[kind]
-    nc = child_size(n, kind)
+    nl, nh, _, _ = KINDS[kind]
+    child_size(n, kind)
     if extent is None:
         extent = (n, n, n)
     for o, x in zip(origin, extent):
         if o % nl or x % nl or not 0 < x <= n or not 0 <= o < n:
             raise ValueError("origin / extent must be multiples of the parent patch inside the box")
     npx, npy, npz = (x // nl for x in extent)
-    # parent cells of the sub-box, periodic
-    ix, iy, iz = ((o + np.arange(x)) % n for o, x in zip(origin, extent))
-    v = parent[np.ix_(ix, iy, iz)].reshape(npx, nl, npy, nl, npz, nl)
-    # parent coefficients a_ijk = sum_mnl F_i(m) F_j(n) F_k(l) V(m, n, l)
-    a_low = np.einsum("im,jn,kl,xmynzl->xiyjzk", f, f, f, v)
-    # every coefficient position takes the child noise at its child cell
-    cx, cy, cz = ((o // nl * nh + np.arange(x // nl * nh)) % nc for o, x in zip(origin, extent))
-    idx = (cx[:, None, None] * nc + cy[None, :, None]) * nc + cz[None, None, :]
-    a = noise_at(seed_child, idx.ravel()).reshape(npx, nh, npy, nh, npz, nh)
-    # ... except the first N_L^3, which are the parent's
-    a[:, :nl, :, :nl, :, :nl] = a_low
-    # W(m, n, l) = sum_ijk a_ijk E_i(m) E_j(n) E_k(l)
-    w = np.einsum("im,jn,kl,xiyjzk->xmynzl", e, e, e, a)
-    return w.reshape(npx * nh, npy * nh, npz * nh)
+    # patch coordinates in the whole grid (periodic), x slowest
+    gx, gy, gz = ((o // nl + np.arange(x // nl)) % (n // nl) for o, x in zip(origin, extent))
+    gp = np.stack(np.meshgrid(gx, gy, gz, indexing="ij"), axis=-1).reshape(-1, 3)
+    # parent values of each patch
+    off = np.arange(nl)
+    px = gp[:, 0, None] * nl + off
+    py = gp[:, 1, None] * nl + off
+    pz = gp[:, 2, None] * nl + off
+    v = parent[px[:, :, None, None], py[:, None, :, None], pz[:, None, None, :]]
+    w = refine_patches(v, kind, seed_child, n, gp)
+    # patches back into the child box
+    return (w.reshape(npx, npy, npz, nh, nh, nh).transpose(0, 3, 1, 4, 2, 5)
+            .reshape(npx * nh, npy * nh, npz * nh))
 
 
 def parent_coefficients(child, kind):

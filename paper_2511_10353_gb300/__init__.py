@@ -64,6 +64,14 @@ class Info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64)]
 
 
+class RefineParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("prec", ctypes.c_int), ("kind", ctypes.c_int),
+                ("origin", ctypes.c_int64 * 3), ("extent", ctypes.c_int64 * 3)]
+
+
+# Appendix A refinement kinds (gg_refine_kind)
+REFINE_KINDS = {"hr": 0, "3/2": 1, "2": 2, "2-linear": 3, "2-sine": 4, "4/3": 5}
+
 _VP3 = ctypes.c_void_p * 3
 
 # name -> (restype, argtypes); mirrors include/gg.h
@@ -108,6 +116,9 @@ _SIGS = {
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "gg_refine_dims": (ctypes.c_int, [ctypes.POINTER(RefineParams), ctypes.POINTER(ctypes.c_int64)]),
+    "gg_refine_noise": (ctypes.c_int, [ctypes.POINTER(RefineParams), ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "gg_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gg_free": (None, [ctypes.c_void_p]),
@@ -231,6 +242,48 @@ def noise_bits(seed, first_group, count, device=None):
     out = torch.empty((int(count), 4), dtype=torch.int32, device=device or "cuda")
     _check(lib().gg_noise_bits(ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(first_group),
                                int(count), out.data_ptr(), _stream_ptr(torch)))
+    return out
+
+
+def refine_params(n, kind="2", prec="f32", origin=(0, 0, 0), extent=None):
+    p = RefineParams()
+    p.n = int(n)
+    p.prec = 1 if prec in ("f64", "fp64", "double") else 0
+    if kind not in REFINE_KINDS:
+        raise ValueError("refinement kind must be one of %s" % sorted(REFINE_KINDS))
+    p.kind = REFINE_KINDS[kind]
+    for j in range(3):
+        p.origin[j] = int(origin[j])
+        p.extent[j] = 0 if extent is None else int(extent[j])
+    return p
+
+
+def refine_dims(n, kind="2", origin=(0, 0, 0), extent=None):
+    """Shape of the child grid of gg_refine_noise."""
+    p = refine_params(n, kind, "f32", origin, extent)
+    dims = (ctypes.c_int64 * 3)()
+    _check(lib().gg_refine_dims(ctypes.byref(p), dims))
+    return tuple(int(d) for d in dims)
+
+
+def refine_noise(parent, seed_child, kind="2", origin=(0, 0, 0), extent=None, out=None):
+    """Appendix A: refined white noise of the box [origin, origin + extent)
+    (parent cells) of the periodic parent grid ``parent`` (n^3, float32 or
+    float64 CUDA tensor). Returns the child grid (a new tensor, or ``out``)."""
+    torch = _torch()
+    n = int(parent.shape[0])
+    prec = "f64" if parent.dtype == torch.float64 else "f32"
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    p = refine_params(n, kind, prec, origin, extent)
+    dims = (ctypes.c_int64 * 3)()
+    _check(lib().gg_refine_dims(ctypes.byref(p), dims))
+    shape = tuple(int(d) for d in dims)
+    src = _dev_ptr(parent, dtype, n ** 3)
+    if out is None:
+        out = torch.empty(shape, dtype=dtype, device=parent.device)
+    dst = _dev_ptr(out, dtype, shape[0] * shape[1] * shape[2])
+    _check(lib().gg_refine_noise(ctypes.byref(p), src, ctypes.c_uint64(int(seed_child) & 0xFFFFFFFFFFFFFFFF),
+                                 dst, _stream_ptr(torch)))
     return out
 
 

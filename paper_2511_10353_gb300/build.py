@@ -31,6 +31,7 @@ SOURCES = [
     "gg_kernels_common.cu",
     "gg_static.cu",
     "gg_cic.cu",
+    "gg_refine.cu",
     "gg_api.cpp",
     "gg_cosmo.cpp",
 ]

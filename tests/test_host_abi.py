@@ -127,3 +127,49 @@ def test_quadrature_is_exact_for_polynomials():
         assert abs(info["growth"] - 1 / (1 + z)) < 1e-13
         assert abs(info["growth_rate"] - 1.0) < 1e-12
         assert abs(info["vfac"] - 100.0 * math.sqrt(1 + z)) < 1e-10
+
+
+@pytest.mark.parametrize("kind,n,origin,extent,want", [
+    ("2", 16, (0, 0, 0), None, (32, 32, 32)),
+    ("3/2", 16, (0, 0, 0), None, (24, 24, 24)),
+    ("4/3", 12, (3, 0, 6), (6, 12, 3), (8, 16, 4)),
+    ("hr", 7, (1, 2, 3), (2, 3, 7), (4, 6, 14)),
+    ("2-sine", 10, (8, 0, 2), (4, 2, 10), (8, 4, 20)),
+])
+def test_refine_dims(kind, n, origin, extent, want):
+    assert gg.refine_dims(n, kind, origin, extent) == want
+
+
+@pytest.mark.parametrize("kind,n,origin,extent", [
+    ("2", 15, (0, 0, 0), None),          # n not a multiple of the parent patch
+    ("4/3", 16, (0, 0, 0), None),
+    ("2", 16, (1, 0, 0), None),          # origin off the patch grid
+    ("2", 16, (16, 0, 0), None),         # origin outside the box
+    ("2", 16, (0, 0, 0), (18, 16, 16)),  # extent larger than the box
+    ("2", 16, (0, 0, 0), (3, 16, 16)),   # extent off the patch grid
+    ("3/2", 16, (0, 0, 0), (16, -2, 16)),
+])
+def test_refine_invalid_rejected(kind, n, origin, extent):
+    p = gg.refine_params(n, kind, "f32", origin, extent)
+    dims = (ctypes.c_int64 * 3)()
+    assert gg.lib().gg_refine_dims(ctypes.byref(p), dims) == gg.GG_EINVAL
+    assert gg.lib().gg_last_error(None)
+    # the same check comes before any device work in gg_refine_noise
+    assert gg.lib().gg_refine_noise(ctypes.byref(p), None, 1, None, None) == gg.GG_EINVAL
+
+
+def test_refine_bad_kind_precision_and_pointers():
+    L = gg.lib()
+    p = gg.refine_params(16, "2")
+    p.kind = 9
+    assert L.gg_refine_dims(ctypes.byref(p), (ctypes.c_int64 * 3)()) == gg.GG_EINVAL
+    p = gg.refine_params(16, "2")
+    p.prec = 3
+    assert L.gg_refine_dims(ctypes.byref(p), (ctypes.c_int64 * 3)()) == gg.GG_EINVAL
+    p = gg.refine_params(16, "2")
+    assert L.gg_refine_dims(None, (ctypes.c_int64 * 3)()) == gg.GG_EINVAL
+    assert L.gg_refine_dims(ctypes.byref(p), None) == gg.GG_EINVAL
+    # NULL or misaligned buffers: rejected before any device call
+    assert L.gg_refine_noise(ctypes.byref(p), None, 1, None, None) == gg.GG_EINVAL
+    assert L.gg_refine_noise(ctypes.byref(p), 4, 1, 4096, None) == gg.GG_EINVAL
+    assert b"aligned" in L.gg_last_error(None)
