@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # capture, scaled to the bench workload, with the hash of the kernel sources it
 # was taken on; reported as null when the sources have changed since.
 NCU_TRAFFIC = {
-    # profiles/x_fused_512_fp32_ncu.md: 556.1 MB read + 1019.7 MB written
-    ("x_fused_filter", "zeldovich_512_fp32"): (1575779328.0, "7e5677d7305ac251"),
+    # profiles/z_inverse_512_fp32_ncu.md: 536,911,104 B read + 1,017,440,000 B written
+    ("z_inverse_epilogue", "zeldovich_512_fp32"): (1554351104.0, "5e75a0ca51f38cd6"),
 }
 
 
@@ -246,11 +246,110 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ white-noise refinement
+REFINE_METRIC = "child grid cells/sec, white-noise refinement (Appendix A), % HBM roofline"
+
+
+def refine_cpu_sample(w, n_s):
+    """The oracle refinement of an n_s^3 parent: (seconds, child cells)."""
+    from oracle import noise, refine
+    parent = noise.white_noise(w["seed_parent"], n_s)
+    t0 = time.perf_counter()
+    child = refine.refine(parent, w["kind"], w["seed_child"])
+    return time.perf_counter() - t0, child.size
+
+
+def run_refine(args):
+    """gg_refine_noise on the workload's parent grid, one launch per step."""
+    import torch
+    import paper_2511_10353_gb300 as gg
+    from paper_2511_10353_gb300 import build
+    from paper_2511_10353_gb300.workloads import BBKS, REFINE_WORKLOADS
+    w = REFINE_WORKLOADS[args.workload]
+    rank, _, world = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n_s = 32  # about 0.3 s per step on one core
+        for _ in range(args.warmup):
+            refine_cpu_sample(w, n_s)
+        total, cells = 0.0, 0
+        for _ in range(args.steps):
+            s, c = refine_cpu_sample(w, n_s)
+            total += s
+            cells += c
+        from oracle.fields import WORKERS
+        value = cells / total
+        print(json.dumps({
+            "impl": "reference", "metric": REFINE_METRIC, "value": value, "unit": "cells/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_parent": w["n"], "kind": w["kind"]},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step one %d^3 parent refined by the numpy oracle"
+                                       % n_s},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    torch.cuda.set_device(0)
+    build.build(verbose=False)
+    n = w["n"]
+    dtype = torch.float32 if w["prec"] == "f32" else torch.float64
+    esz = 4 if w["prec"] == "f32" else 8
+    plan = gg.Plan(n, float(n), BBKS, 50.0, w["prec"])
+    parent = plan.white_noise(seed=w["seed_parent"])
+    plan.sync()
+    plan.close()
+    dims = gg.refine_dims(n, w["kind"])
+    child = torch.empty(dims, dtype=dtype, device="cuda")
+    cells = dims[0] * dims[1] * dims[2]
+    for i in range(max(3, args.warmup)):
+        gg.refine_noise(parent, w["seed_child"] + i, w["kind"], out=child)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        gg.refine_noise(parent, w["seed_child"] + i, w["kind"], out=child)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = cells / (ms * 1e-3)
+    nbytes = esz * (n ** 3 + cells)  # parent read once, child written once
+    peak, src = peak_hbm()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    line = {"metric": REFINE_METRIC, "value": value, "unit": "cells/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": w["prec"], "data": "synthetic",
+            "config": {"workload": args.workload, "n_parent": n, "child_dims": list(dims),
+                       "kind": w["kind"], "cells_per_step": cells,
+                       "l2": "working set > L2 (129 MB), no flush"},
+            "roofline": {"bound": "hbm", "kernel": "k_refine", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+                         "algorithmic_bytes_per_launch": nbytes, "traffic": None},
+            "gpu_launches": args.steps, "clocks": clocks, "e2e": None}
+    if not args.no_cpu_baseline:
+        secs, c = refine_cpu_sample(w, 64)
+        line["cpu_baseline"] = {"value": c / secs, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                "sample": "one 64^3 parent refined by the numpy oracle (%.1f s)"
+                                          % secs}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
     if args.workload == "batched_48" and args.impl == "ours":
         run_batched(args)
+        return
+    if args.workload.startswith("refine_"):
+        run_refine(args)
         return
     from paper_2511_10353_gb300.workloads import WORKLOADS
     w = dict(WORKLOADS[args.workload])

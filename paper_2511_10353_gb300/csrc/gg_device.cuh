@@ -66,34 +66,29 @@ __device__ __forceinline__ uint4 noise_words(uint64_t seed, uint64_t group) {
                        (uint32_t)(seed >> 32));
 }
 
-// Two-output Box-Muller (Box & Muller 1958) on each word pair of a group:
+// Two-output Box-Muller (Box & Muller 1958) on one word pair (r_a, r_b):
 // u_a = (r_a + 1) 2^-32 in (0, 1], u_b = r_b 2^-32; rho = sqrt(-2 ln u_a);
-// outputs rho cos(2 pi u_b), rho sin(2 pi u_b).
-__device__ __forceinline__ void gauss4(uint4 w, float out[4]) {
-  const float ua0 = fmaf(__uint2float_rn(w.x), 0x1p-32f, 0x1p-32f);
-  const float ua1 = fmaf(__uint2float_rn(w.z), 0x1p-32f, 0x1p-32f);
-  const float rho0 = sqrtf(-2.0f * logf(ua0));
-  const float rho1 = sqrtf(-2.0f * logf(ua1));
-  float s0, c0, s1, c1;
-  sincospif(2.0f * (__uint2float_rn(w.y) * 0x1p-32f), &s0, &c0);
-  sincospif(2.0f * (__uint2float_rn(w.w) * 0x1p-32f), &s1, &c1);
-  out[0] = rho0 * c0;
-  out[1] = rho0 * s0;
-  out[2] = rho1 * c1;
-  out[3] = rho1 * s1;
+// outputs rho cos(2 pi u_b), rho sin(2 pi u_b). gauss4 applies it to the
+// pairs (r0, r1) and (r2, r3) of a group.
+__device__ __forceinline__ void gauss2(uint32_t ra, uint32_t rb, float &c, float &s) {
+  const float ua = fmaf(__uint2float_rn(ra), 0x1p-32f, 0x1p-32f);
+  const float rho = sqrtf(-2.0f * logf(ua));
+  float sn, cs;
+  sincospif(2.0f * (__uint2float_rn(rb) * 0x1p-32f), &sn, &cs);
+  c = rho * cs;
+  s = rho * sn;
 }
-__device__ __forceinline__ void gauss4(uint4 w, double out[4]) {
-  const double ua0 = ((double)w.x + 1.0) * 0x1p-32;
-  const double ua1 = ((double)w.z + 1.0) * 0x1p-32;
-  const double rho0 = sqrt(-2.0 * log(ua0));
-  const double rho1 = sqrt(-2.0 * log(ua1));
-  double s0, c0, s1, c1;
-  sincospi(2.0 * ((double)w.y * 0x1p-32), &s0, &c0);
-  sincospi(2.0 * ((double)w.w * 0x1p-32), &s1, &c1);
-  out[0] = rho0 * c0;
-  out[1] = rho0 * s0;
-  out[2] = rho1 * c1;
-  out[3] = rho1 * s1;
+__device__ __forceinline__ void gauss2(uint32_t ra, uint32_t rb, double &c, double &s) {
+  const double ua = ((double)ra + 1.0) * 0x1p-32;
+  const double rho = sqrt(-2.0 * log(ua));
+  double sn, cs;
+  sincospi(2.0 * ((double)rb * 0x1p-32), &sn, &cs);
+  c = rho * cs;
+  s = rho * sn;
+}
+template <typename R> __device__ __forceinline__ void gauss4(uint4 w, R out[4]) {
+  gauss2(w.x, w.y, out[0], out[1]);
+  gauss2(w.z, w.w, out[2], out[3]);
 }
 
 // W at one cell (used where a line does not start on a group boundary).

@@ -40,15 +40,17 @@ struct RefineBox {
 };
 
 // N_H consecutive child-noise values starting at global child cell idx0
-// (they lie in one or two Philox groups).
-template <typename R, int NH>
+// (they lie in one or two Philox groups). HI_ONLY (runs of four): only the
+// last two values are used, so only the second Box-Muller pair is formed.
+template <typename R, int NH, bool HI_ONLY>
 __device__ __forceinline__ void noise_run(uint64_t seed, uint64_t idx0, R out[NH]) {
-  R w[8];
-  gauss4(noise_words(seed, idx0 >> 2), w);
   if constexpr (NH == 4) {  // runs of four start on a group (the host checks nc % 4 == 0)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = w[k];
+    const uint4 g = noise_words(seed, idx0 >> 2);
+    if (!HI_ONLY) gauss2(g.x, g.y, out[0], out[1]);
+    gauss2(g.z, g.w, out[2], out[3]);
   } else {
+    R w[8];
+    gauss4(noise_words(seed, idx0 >> 2), w);
     const int s = (int)(idx0 & 3);
     if (s + NH > 4) {
       gauss4(noise_words(seed, (idx0 >> 2) + 1), w + 4);
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(256) k_refine(const R *__restrict__ parent, R 
             ((uint64_t)(gx * NH + i) * (uint64_t)b.nc + (uint64_t)(gy * NH + j)) * (uint64_t)b.nc +
             (uint64_t)(gz * NH);
         R r[NH];
-        noise_run<R, NH>(seed, idx0, r);
+        if (i < NL && j < NL) noise_run<R, NH, NL >= 2>(seed, idx0, r);  // k < N_L: parent's
+        else noise_run<R, NH, false>(seed, idx0, r);
 #pragma unroll
         for (int k = 0; k < NH; ++k)
           if (i >= NL || j >= NL || k >= NL) a[i][j][k] = r[k];

@@ -38,3 +38,13 @@ def batched_realizations(count=48, sizes=(128, 192, 256, 384)):
         n = sizes[i % len(sizes)]
         out.append(dict(n=n, box=float(n), cosmo=BBKS, z_init=50.0, seed=i + 1, prec="f32"))
     return out
+
+
+# Appendix A white-noise refinement: a 768^3 parent (Philox white noise,
+# seed 1) doubled to the 1536^3 grid of the largest Zel'dovich workload with
+# the bases of Eqs. A.10-A.13; new coefficients from seed 2.
+REFINE_WORKLOADS = {
+    "refine_768_1536_fp32": dict(n=768, kind="2", prec="f32", seed_parent=1, seed_child=2),
+    # the same at an eighth of the size (profiling captures)
+    "refine_384_768_fp32": dict(n=384, kind="2", prec="f32", seed_parent=1, seed_child=2),
+}
