@@ -73,11 +73,19 @@ __device__ __forceinline__ int k_of(int p, int b) {
   }
 }
 
+// Barrier of an in-place stage: none (the stage writes elsewhere), the whole
+// CTA, or the warp (when every transform lies within one warp).
+enum Sync : int { kSyncNone = 0, kSyncCta = 1, kSyncWarp = 2 };
+template <int SY> __device__ __forceinline__ void stage_barrier() {
+  if constexpr (SY == kSyncCta) __syncthreads();
+  else if constexpr (SY == kSyncWarp) __syncwarp();
+}
+
 // One Stockham stage of a length-N transform, stage index SI of the forward
 // (INV = false) or inverse schedule, for the butterflies j = p + P*b of this
 // thread. ld(n) reads element n of the stage input, st(n, v) writes element n
-// of its output; with SYNC the stage runs in place in shared memory.
-template <typename R, int N, int E, int SI, bool INV, bool SYNC, class Ld, class St>
+// of its output; with a barrier (SY) the stage runs in place in shared memory.
+template <typename R, int N, int E, int SI, bool INV, int SY, class Ld, class St>
 __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                       const St &st) {
   constexpr int RAD = radix_of(N, SI, INV);
@@ -94,7 +102,7 @@ __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const
   for (int b = 0; b < NB; ++b)
 #pragma unroll
     for (int r = 0; r < RAD; ++r) v[b * RAD + r] = ld(p + P * b + r * SPAN);
-  if (SYNC) __syncthreads();
+  stage_barrier<SY>();
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if constexpr (NS > 1) {
@@ -118,16 +126,17 @@ __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const
 #pragma unroll
     for (int r = 0; r < RAD; ++r) st(base + r * NS, v[b * RAD + r]);
   }
-  if (SYNC) __syncthreads();
+  stage_barrier<SY>();
 }
 
-// Stages FIRST .. LAST-1 in place in shared memory.
-template <typename R, int N, int E, bool INV, int FIRST, int LAST, class Ld, class St>
+// Stages FIRST .. LAST-1 in place in shared memory, barrier SY.
+template <typename R, int N, int E, bool INV, int FIRST, int LAST, int SY = kSyncCta, class Ld,
+          class St>
 __device__ __forceinline__ void stages(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                        const St &st) {
   if constexpr (FIRST < LAST) {
-    stage<R, N, E, FIRST, INV, true>(p, tw, ld, st);
-    stages<R, N, E, INV, FIRST + 1, LAST>(p, tw, ld, st);
+    stage<R, N, E, FIRST, INV, SY>(p, tw, ld, st);
+    stages<R, N, E, INV, FIRST + 1, LAST, SY>(p, tw, ld, st);
   }
 }
 
@@ -202,13 +211,27 @@ template <typename R, int N, int V> struct AxisPolicy {
 };
 
 // z passes: lines per tile, variant 0 ~256 threads (sized so that two dense
-// tiles and a padded tile fit in 160 KB), variant 1 half as many lines.
+// tiles and a padded tile fit in 160 KB), variant 1 half as many lines,
+// variant 2 the lines of variant 0 with warp instead of CTA barriers between
+// the stages (where each line lies within one warp; warps then drift apart).
 template <typename R, int N, int V> struct ZPolicy {
   static constexpr int M = N / 2;
   static constexpr int E = elems(M);
   static constexpr int P = M / E;
   static constexpr int CB = 2 * (int)sizeof(R);
-  static constexpr int LD = M + (M >> 4) + 1;
+  static constexpr int LD = M + (M >> 4) + 1;  // tile sizing (the widest padding)
+  // Padding of the work tile, per direction: one empty slot every PAD values
+  // (0: none). Chosen by counting the shared-memory wavefronts of every
+  // stage's stores and loads for each size; FP32 (FP64 keeps 1 in 16).
+  static constexpr int pad_of(bool inv) {
+    if (sizeof(R) != 4) return 16;
+    if (M == 96) return 32;           // N = 192: 1.2x / 1.5x the minimum instead of 2x
+    if (inv && M == 768) return 0;    // N = 1536 inverse: 1.25x instead of 1.48x
+    return 16;
+  }
+  static constexpr int PAD_INV = pad_of(true), PAD_FWD = pad_of(false);
+  static constexpr int LD_INV = M + (PAD_INV ? M / PAD_INV : 0) + 1;
+  static constexpr int LD_FWD = M + (PAD_FWD ? M / PAD_FWD : 0) + 1;
   static constexpr int pick() {
     int l = 1;
     while (l < 64 && P * l * 2 <= 256 && (2 * (2 * l) * M + 2 * l * LD) * CB <= 160 * 1024) l *= 2;
@@ -217,8 +240,12 @@ template <typename R, int N, int V> struct ZPolicy {
   }
   static constexpr int L = pick();
   static constexpr int THREADS = P * L;
+  // variant 2, and every line within one warp (P divides 32): the stages need
+  // only warp barriers
+  static constexpr int SY = (V == 2 && P <= 32 && 32 % P == 0) ? kSyncWarp : kSyncCta;
   static constexpr int DENSE = L * M;        // complex values of one dense tile
-  static constexpr int WORK = L * LD;        // complex values of the padded tile
+  static constexpr int WORK_INV = L * LD_INV;  // complex values of the padded tiles
+  static constexpr int WORK_FWD = L * LD_FWD;
   // CTAs per SM the register allocation must leave room for: enough for 16
   // warps, as far as the shared memory of the pass allows (inverse: a dense
   // staging tile and the padded tile; forward: the padded tile). FP64 lines
@@ -228,8 +255,8 @@ template <typename R, int N, int V> struct ZPolicy {
     const int m = by_smem < by_warps ? by_smem : by_warps;
     return sizeof(R) == 4 && m > 0 ? m : 1;
   }
-  static constexpr int MINB_INV = min_blocks(128 + DENSE * CB + WORK * CB);
-  static constexpr int MINB_FWD = min_blocks(WORK * CB);
+  static constexpr int MINB_INV = min_blocks(128 + DENSE * CB + WORK_INV * CB);
+  static constexpr int MINB_FWD = min_blocks(WORK_FWD * CB);
 };
 
 }  // namespace ct

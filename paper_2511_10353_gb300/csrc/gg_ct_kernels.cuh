@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
           for (int r = 0; r < RH; ++r) buf[((p + P * b) * RH + r) * B + c] = W[b * RH + r];
         __syncthreads();
         ct::stages<R, N, E, true, 1, S - 1>(p, tw, ld_smem, st_smem);
-        ct::stage<R, N, E, S - 1, true, false>(p, tw, ld_smem, st_glob);
+        ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_smem, st_glob);
       }
     }
     __syncthreads();
@@ -190,8 +190,12 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
 
 // ------------------------------------------------------------ z passes
 // Padded line layout of the z-pass work tile: element n of line l at
-// l * LD + n + n / 16 (pairs (2q, 2q+1) never straddle a pad).
-template <int LD> __device__ __forceinline__ int zpad(int l, int n) { return l * LD + n + (n >> 4); }
+// l * LD + n + n / PAD (PAD a power of two or 0: no padding; pairs
+// (2q, 2q+1) never straddle a pad).
+template <int LD, int PAD> __device__ __forceinline__ int zpad(int l, int n) {
+  if constexpr (PAD == 0) return l * LD + n;
+  else return l * LD + n + (int)((unsigned)n / PAD);
+}
 
 // Inverse z pass (c2r) + Eq. 3 epilogue, persistent: one thread bulk-copies
 // a block of L contiguous half-spectrum lines into a dense shared buffer. The
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     k_zinv_ct(const ZInvArgs a) {
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
-  constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
+  constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD_INV, PAD = Pol::PAD_INV;
   constexpr int S = ct::nstages(M);
   constexpr int RL = ct::radix_of(M, S - 1, true), SPANL = M / RL, NBL = E / RL;
   constexpr int DENSE_STRIDE = (int)(((Pol::DENSE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
@@ -247,16 +251,16 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       }
       const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
       const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
-      work[zpad<LD>(l, k)] = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
+      work[zpad<LD, PAD>(l, k)] = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
     }
     __syncthreads();
     if (tid == 0 && tn < ntiles) {  // the dense buffer has been read: fetch the next block
       fence_proxy_async_smem();
       issue(tn);
     }
-    auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
-    auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
-    ct::stages<R, M, E, true, 0, S - 1>(p, tw_half, ld_w, st_w);
+    auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
+    auto st_w = [&](int n, C v) { work[zpad<LD, PAD>(l, n)] = v; };
+    ct::stages<R, M, E, true, 0, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
     C v[E];
     ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
     const int64_t line = t * L + l;
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
         }
         if (vel) vel[n] = C{vfac * z.x, vfac * z.y};
       }
-    __syncthreads();
+    ct::stage_barrier<Pol::SY>();  // the work tile's lines are rewritten next tile
   }
 }
 
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     k_zfwd_ct(const ZFwdArgs a) {
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
-  constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD;
+  constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD_FWD, PAD = Pol::PAD_FWD;
   constexpr int S = ct::nstages(M);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C *work = reinterpret_cast<C *>(smem_raw);
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     if (a.noise) {
       const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
 #pragma unroll
-      for (int i = 0; i < E; ++i) work[zpad<LD>(l, p + P * i)] = src[p + P * i];
+      for (int i = 0; i < E; ++i) work[zpad<LD, PAD>(l, p + P * i)] = src[p + P * i];
     } else {
       static_assert(N % 4 == 0, "lines start on a Philox group");
       const uint64_t g0 = (uint64_t)local * (uint64_t)(N / 4);
@@ -334,25 +338,25 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
         const int q = p + P * i;
         R w[4];
         gauss4(noise_words(seed, g0 + q), w);
-        work[zpad<LD>(l, 2 * q)] = C{w[0], w[1]};
-        work[zpad<LD>(l, 2 * q + 1)] = C{w[2], w[3]};
+        work[zpad<LD, PAD>(l, 2 * q)] = C{w[0], w[1]};
+        work[zpad<LD, PAD>(l, 2 * q + 1)] = C{w[2], w[3]};
       }
     }
-    __syncthreads();
-    auto ld_w = [&](int n) { return work[zpad<LD>(l, n)]; };
-    auto st_w = [&](int n, C v) { work[zpad<LD>(l, n)] = v; };
-    ct::stages<R, M, E, false, 0, S>(p, tw_half, ld_w, st_w);
+    ct::stage_barrier<Pol::SY>();
+    auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
+    auto st_w = [&](int n, C v) { work[zpad<LD, PAD>(l, n)] = v; };
+    ct::stages<R, M, E, false, 0, S, Pol::SY>(p, tw_half, ld_w, st_w);
     C *dst = reinterpret_cast<C *>(a.out) + line * M;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k = p + P * i;
-      const C zk = work[zpad<LD>(l, k)];
-      const C zm = work[zpad<LD>(l, k ? M - k : 0)];
+      const C zk = work[zpad<LD, PAD>(l, k)];
+      const C zm = work[zpad<LD, PAD>(l, k ? M - k : 0)];
       const C fe = {(R)0.5 * (zk.x + zm.x), (R)0.5 * (zk.y - zm.y)};
       const C fo = {(R)0.5 * (zk.y + zm.y), (R)-0.5 * (zk.x - zm.x)};
       dst[k] = cadd(fe, cmul(fo, ldg_c(twf + k)));
     }
-    __syncthreads();
+    ct::stage_barrier<Pol::SY>();  // the work tile's lines are rewritten next tile
   }
 }
 
@@ -383,7 +387,7 @@ template <typename R, int N, int V>
 cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
   using Pol = ct::ZPolicy<R, N, V>;
   const size_t dense = (Pol::DENSE * 2 * sizeof(R) + 127) & ~(size_t)127;
-  const size_t smem = 128 + dense + (size_t)Pol::WORK * 2 * sizeof(R);
+  const size_t smem = 128 + dense + (size_t)Pol::WORK_INV * 2 * sizeof(R);
   auto kern = k_zinv_ct<R, N, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -394,7 +398,7 @@ cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
 template <typename R, int N, int V>
 cudaError_t ct_launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
   using Pol = ct::ZPolicy<R, N, V>;
-  const size_t smem = (size_t)Pol::WORK * 2 * sizeof(R);
+  const size_t smem = (size_t)Pol::WORK_FWD * 2 * sizeof(R);
   auto kern = k_zfwd_ct<R, N, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -403,7 +407,7 @@ cudaError_t ct_launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
 }
 
 constexpr int kAxisVariants = 3;
-constexpr int kZVariants = 2;
+constexpr int kZVariants = 3;
 
 // Run-time dispatch over the specialised sizes and their tile variants.
 template <typename R, int... NS> struct CtTable {
@@ -426,16 +430,22 @@ template <typename R, int... NS> struct CtTable {
     ((a.n == NS ? (e = axis_n<NS>(a, s), 0) : 0), ...);
     return e;
   }
+  template <int N> static cudaError_t zinv_n(const ZInvArgs &a, cudaStream_t s) {
+    return a.variant == 1 ? ct_launch_zinv<R, N, 1>(a, s)
+                          : (a.variant == 2 ? ct_launch_zinv<R, N, 2>(a, s) : ct_launch_zinv<R, N, 0>(a, s));
+  }
+  template <int N> static cudaError_t zfwd_n(const ZFwdArgs &a, cudaStream_t s) {
+    return a.variant == 1 ? ct_launch_zfwd<R, N, 1>(a, s)
+                          : (a.variant == 2 ? ct_launch_zfwd<R, N, 2>(a, s) : ct_launch_zfwd<R, N, 0>(a, s));
+  }
   static cudaError_t zinv(const ZInvArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;
-    ((a.n == NS ? (e = a.variant == 1 ? ct_launch_zinv<R, NS, 1>(a, s) : ct_launch_zinv<R, NS, 0>(a, s), 0)
-                : 0), ...);
+    ((a.n == NS ? (e = zinv_n<NS>(a, s), 0) : 0), ...);
     return e;
   }
   static cudaError_t zfwd(const ZFwdArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;
-    ((a.n == NS ? (e = a.variant == 1 ? ct_launch_zfwd<R, NS, 1>(a, s) : ct_launch_zfwd<R, NS, 0>(a, s), 0)
-                : 0), ...);
+    ((a.n == NS ? (e = zfwd_n<NS>(a, s), 0) : 0), ...);
     return e;
   }
 };
