@@ -1287,10 +1287,13 @@ void gg_free(gg_plan_t *plan) {
 gg_status gg_batch_plan(gg_batch_t **batch, const gg_params *params, int count, void *stream) {
   if (!batch || !params || count < 1) return fail(nullptr, GG_EINVAL, "bad batch arguments");
   *batch = nullptr;
+  int64_t lines = 0;  // the batched kernels index lines with 32-bit integers
   for (int i = 0; i < count; ++i) {
     const std::string msg = validate(&params[i]);
     if (!msg.empty()) return fail(nullptr, GG_EINVAL, "realization " + std::to_string(i) + ": " + msg);
+    lines += params[i].n * params[i].n;
   }
+  if (lines >= ((int64_t)1 << 31)) return fail(nullptr, GG_EINVAL, "batch too large (N^2 summed >= 2^31)");
   gg_batch_t *b = new (std::nothrow) gg_batch_t();
   if (!b) return fail(nullptr, GG_ENOMEM, "host allocation failed");
   b->count = count;

@@ -240,14 +240,16 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     const bool ok = __syncthreads_and(mbar_wait(bar, (uint32_t)(it & 1), a.err));
     if (!ok) return;  // nothing else in flight: the next copy is issued after this wait
     const C *dl = dense + l * M;
+    const R pf = (R)p;  // (R)(p + c) == pf + (R)c exactly: small integers
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k = p + P * i;
       C xk = dl[k];
       C xm = k ? dl[M - k] : C{(R)0, (R)0};
       if (a.mul_kz) {  // i m_z on both members of the pair
-        xk = C{-(R)k * xk.y, (R)k * xk.x};
-        xm = C{-(R)(M - k) * xm.y, (R)(M - k) * xm.x};
+        const R kf = pf + (R)(P * i), mf = (R)M - kf;
+        xk = C{-kf * xk.y, kf * xk.x};
+        xm = C{-mf * xm.y, mf * xm.x};
       }
       const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
       const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
@@ -263,15 +265,18 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     ct::stages<R, M, E, true, 0, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
     C v[E];
     ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
-    const int64_t line = t * L + l;
-    const int64_t lpr = a.lines_per_real > 0 ? a.lines_per_real : a.nlines;
-    const int64_t rr = line / lpr, local = line - rr * lpr;
-    const int64_t ix = local / a.n, iy = local - ix * a.n;
+    // line -> (realization, x, y): line counts stay below 2^32 (N <= 4096, the
+    // host bounds the batch), so 32-bit divisions suffice
+    const uint32_t line = (uint32_t)(t * L + l);
+    const uint32_t lpr = (uint32_t)(a.lines_per_real > 0 ? a.lines_per_real : a.nlines);
+    const uint32_t rr = line / lpr, local = line - rr * lpr;
+    const uint32_t ix = local / (uint32_t)a.n, iy = local - ix * (uint32_t)a.n;
     const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
+    const R q2p = (R)(2 * p);  // (R)(2n) == q2p + (R)(2n - 2p) exactly
     void *psi_b = a.psi_list ? a.psi_list[rr] : a.psi;
     void *pos_b = a.pos_list ? a.pos_list[rr] : a.pos;
     void *vel_b = a.vel_list ? a.vel_list[rr] : a.vel;
-    const int64_t off = (a.psi_list || a.pos_list || a.vel_list) ? local * M : line * M;
+    const int64_t off = (int64_t)((a.psi_list || a.pos_list || a.vel_list) ? local : line) * M;
     C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
     C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
     C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
@@ -292,8 +297,8 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
         if (pos) {
           R q0 = qline, q1 = qline;
           if (a.comp == 2) {
-            q0 = ((R)(2 * n) + qo) * cell;
-            q1 = ((R)(2 * n + 1) + qo) * cell;
+            q0 = (q2p + (R)(2 * (n - p)) + qo) * cell;
+            q1 = (q2p + (R)(2 * (n - p) + 1) + qo) * cell;
           }
           pos[n] = C{wrap_box<R>(q0 + z.x, box), wrap_box<R>(q1 + z.y, box)};
         }
@@ -323,8 +328,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     int l = tid / P, p = tid - (tid / P) * P;
     asm volatile("" : "+r"(l), "+r"(p));
     const int64_t line = t * L + l;
-    const int64_t lpr = a.lines_per_real > 0 ? a.lines_per_real : a.nlines;
-    const int64_t rr = line / lpr, local = line - rr * lpr;
+    // line counts stay below 2^32 (N <= 4096, the host bounds the batch)
+    const uint32_t lpr = (uint32_t)(a.lines_per_real > 0 ? a.lines_per_real : a.nlines);
+    const uint32_t rr = (uint32_t)line / lpr, local = (uint32_t)line - rr * lpr;
     const uint64_t seed = a.seeds ? a.seeds[rr] : a.seed;
     if (a.noise) {
       const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
