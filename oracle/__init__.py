@@ -20,7 +20,10 @@ computes (Ginnungagap, arXiv:2511.10353):
                 with numpy/scipy FFTs as the transform step.
 * ``adjoint``   The transpose of the linear map W -> psi and of the CIC /
                 smoothing chain used for gradient checks.
-* ``refine``    Appendix A white-noise refinement (Eqs. A.1-A.19).
+* ``refine``    Appendix A white-noise refinement (Eqs. A.1-A.28).
+* ``merge``     Sec. 2.4: large scales of a coarse field (Eq. 5, with the
+                cloud-in-cell deconvolution and interpolation) plus small
+                scales of a fine one (Eq. 4), then Eq. 3.
 
 Every function states the passage it follows. Where the paper is silent the
 reading taken is stated at the function. Parity is pinned in
