@@ -302,6 +302,30 @@ gg_status gg_cic_density(gg_plan_t *plan, const void *const psi_dev[3], void *de
 gg_status gg_cic_density_adjoint(gg_plan_t *plan, const void *const psi_dev[3],
                                  const void *g_delta_dev, void *const g_psi_dev[3]);
 
+/* ------------------------------------------------------- large/small-scale merge
+ * Sec. 2.4, Eqs. 4-5: the velocity field of a refined (high-resolution)
+ * white noise takes its small scales from the fine grid and its large scales
+ * from the coarse grid's field. k is the angular wavenumber 2 pi m / L; the
+ * spherical top hat f(|k| r_s) = [|k| r_s < 1] splits them (the paper takes
+ * r_s = 2 L / N_low). Grid values sit at cell centres. */
+
+/* Eq. 5 with the cloud-in-cell deconvolution, on a real field of the plan's
+ * grid: out = F^-1[ f(|k| r_s) F[in] / prod_j sinc^2(pi m_j / N) ] (modes with
+ * any |m_j| = N/2 dropped). in_dev, out_dev: N^3 reals, 16-byte aligned,
+ * caller-owned, may be the same buffer. Uses the plan's workspace. */
+gg_status gg_large_scales(gg_plan_t *plan, double r_s, const void *in_dev, void *out_dev);
+
+/* gg_zeldovich with Eq. 4 and the merge: the displacement of the plan's
+ * grid keeps only modes with |k| r_s >= 1, then the cloud-in-cell
+ * (trilinear, periodic, between cell centres) interpolation of the coarse
+ * grid large_dev[j] (n_low^3 reals, e.g. gg_large_scales of a coarse plan's
+ * psi_j) is added before the Eq. 3 epilogue; psi, pos and vel are those of
+ * the merged displacement. NULL large_dev entries add nothing. Other
+ * arguments as gg_zeldovich; 1 <= n_low <= n. */
+gg_status gg_zeldovich_merge(gg_plan_t *plan, uint64_t seed, const void *noise_dev, double r_s,
+                             int64_t n_low, const void *const large_dev[3], void *const psi_dev[3],
+                             void *const pos_dev[3], void *const vel_dev[3]);
+
 /* ---------------------------------------------------------------- refinement
  * Appendix A: a white-noise field of higher resolution whose large scales are
  * those of a given parent field. Each patch of N_L parent cells per axis is

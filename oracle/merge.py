@@ -24,6 +24,8 @@ Readings taken where the section is silent:
   triangle of half-width one coarse cell, whose transform is
   sinc^2(k_j Delta / 2) = [sin(pi m_j / N_low) / (pi m_j / N_low)]^2; the
   deconvolution divides by the product over the three axes.
+* Modes with any |m_j| = N/2 are dropped, as everywhere on this path (they
+  matter only for cutoffs below about a third of a cell).
 * The Zel'dovich epilogue (Eq. 3) is applied to the merged displacement,
   so positions and velocities follow from it as in ``fields.zeldovich``.
 """
@@ -50,7 +52,9 @@ def large_scales(field, box, r_s):
     """Eq. 5 with the deconvolution: F^-1[f(|k| r_s) F[field] / W_CIC]."""
     n = field.shape[0]
     fk = np.fft.rfftn(np.asarray(field, dtype=np.float64))
-    fk = np.where(low_modes(n, box, r_s), fk / cic_window(n), 0.0)
+    mx, my, mz = fields.integer_modes(n)
+    no_nyquist = (np.abs(mx) != n // 2) & (np.abs(my) != n // 2) & (mz != n // 2)
+    fk = np.where(low_modes(n, box, r_s) & no_nyquist, fk / cic_window(n), 0.0)
     return np.fft.irfftn(fk, s=field.shape, axes=(0, 1, 2))
 
 

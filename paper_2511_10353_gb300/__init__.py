@@ -116,6 +116,11 @@ _SIGS = {
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "gg_large_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "gg_zeldovich_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_refine_dims": (ctypes.c_int, [ctypes.POINTER(RefineParams), ctypes.POINTER(ctypes.c_int64)]),
     "gg_refine_noise": (ctypes.c_int, [ctypes.POINTER(RefineParams), ctypes.c_void_p, ctypes.c_uint64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
@@ -351,6 +356,32 @@ class Plan:
         self._bind_stream()
         _check(lib().gg_zeldovich(self._h, ctypes.c_uint64(int(seed)),
                                   _dev_ptr(noise, self.dtype, self._cells()), *arrs), self._h)
+        return out
+
+    def large_scales(self, field, r_s, out=None):
+        """Sec. 2.4, Eq. 5 with the cloud-in-cell deconvolution of a real field."""
+        out = self.empty() if out is None else out
+        self._bind_stream()
+        _check(lib().gg_large_scales(self._h, float(r_s), _dev_ptr(field, self.dtype, self._cells()),
+                                     _dev_ptr(out, self.dtype, self._cells())), self._h)
+        return out
+
+    def zeldovich_merge(self, large, r_s, seed=0, noise=None, psi=True, pos=True, vel=True,
+                        out=None):
+        """Sec. 2.4: gg_zeldovich keeping modes with |k| r_s >= 1 (Eq. 4) plus the
+        cloud-in-cell interpolation of the coarse grids ``large`` (three n_low^3
+        tensors or None, Eq. 5 already applied, e.g. by ``large_scales``)."""
+        n_low = next((int(t.shape[0]) for t in large if t is not None), 1)
+        if out is None:
+            out = {k: [self.empty() for _ in range(3)] if want else [None] * 3
+                   for k, want in (("psi", psi), ("pos", pos), ("vel", vel))}
+        lg = _VP3(*[None if t is None else _dev_ptr(t, self.dtype, n_low ** 3) for t in large])
+        arrs = [_VP3(*[_dev_ptr(t, self.dtype, self._cells()) for t in out[k]])
+                for k in ("psi", "pos", "vel")]
+        self._bind_stream()
+        _check(lib().gg_zeldovich_merge(self._h, ctypes.c_uint64(int(seed)),
+                                        _dev_ptr(noise, self.dtype, self._cells()), float(r_s),
+                                        n_low, lg, *arrs), self._h)
         return out
 
     def zeldovich_host(self, seed=0, noise=None, psi=True, pos=True, vel=True, out=None):

@@ -32,6 +32,7 @@ SOURCES = [
     "gg_static.cu",
     "gg_cic.cu",
     "gg_refine.cu",
+    "gg_merge.cu",
     "gg_api.cpp",
     "gg_cosmo.cpp",
 ]

@@ -43,6 +43,7 @@ struct Tables {
   // FP32 shared-memory forms of the three filters (see AxisArgs::interp)
   void *interp_u = nullptr, *interp_s = nullptr, *interp_smooth = nullptr;
   int interp_cells = 0;
+  void *cic_deconv = nullptr;  // N reals: 1 / sinc^2(pi m_i / N) per array index (Sec. 2.4)
 };
 
 }  // namespace
@@ -80,6 +81,12 @@ struct gg_plan {
   double prof_ms[16] = {0};
   int64_t prof_launches[16] = {0};
   double prof_bytes[16] = {0};
+  // Sec. 2.4 merge, set for the duration of gg_zeldovich_merge: top hat on the
+  // x pass (modes with m2 < merge_qmin dropped) and the coarse grids whose
+  // interpolation the z inverse passes add
+  int merge_qmin = 0;
+  const void *merge_large[3] = {nullptr, nullptr, nullptr};
+  int merge_nlow = 0;
 };
 
 struct gg_batch {
@@ -333,7 +340,7 @@ void release(gg_plan_t *plan) {
                   plan->tab.tw_n,    plan->tab.tw_half,   plan->tab.s_delta,
                   plan->tab.u_phi,   plan->err,           plan->noise_stage,
                   plan->tab.smooth,  plan->tab.interp_u,  plan->tab.interp_s,
-                  plan->tab.interp_smooth};
+                  plan->tab.interp_smooth, plan->tab.cic_deconv};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (auto &slot : plan->stage)
@@ -489,6 +496,8 @@ gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void 
   z.tw_full = plan->tab.tw_n;
   z.err = plan->err;
   z.variant = plan->variant[5];
+  z.large = plan->merge_large[comp];
+  z.n_low = plan->merge_nlow;
   const double cb = (double)plan->cells * sizeof(R);
   const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
   cudaError_t e;
@@ -537,6 +546,7 @@ gg_status spectral_passes(gg_plan_t *plan, uint64_t seed, const void *noise, con
   x.table = plan->tab.u_phi;
   x.interp = plan->tab.interp_u;
   x.interp_cells = plan->tab.interp_cells;
+  x.qmin = plan->merge_qmin;
   x.nout = 0;
   if (want[0]) {
     x.dst[x.nout] = plan->work;
@@ -819,6 +829,61 @@ gg_status run_smooth(gg_plan_t *plan, double radius, const void *in, void *out) 
     }
   }
   return run_density<R>(plan, 0, in, out, plan->tab.smooth, plan->tab.interp_smooth);
+}
+
+// Sec. 2.4, Eq. 5 with the cloud-in-cell deconvolution: out = F^-1[f(|k| r_s)
+// F[in] / W_CIC]. Forward z, y and x passes, the spectrum multiplied by the
+// top hat and 1 / prod_j sinc^2(pi m_j / N) (and 1 / N^3), inverse x, y, z.
+int64_t top_hat_qmax(double box, double r_s) {
+  // |k| r_s < 1  <=>  m2 < X = (L / (2 pi r_s))^2  <=>  m2 < ceil(X) (integer m2)
+  const double x = box / (2.0 * kPi * r_s);
+  return (int64_t)std::ceil(x * x);
+}
+
+template <typename R>
+gg_status run_large_scales(gg_plan_t *plan, double r_s, const void *in, void *out) {
+  const int n = (int)plan->p.n;
+  if (!plan->tab.cic_deconv) {
+    std::vector<R> d(n);
+    for (int i = 0; i < n; ++i) {
+      const int m = i < n / 2 ? i : i - n;
+      const double x = kPi * m / n;
+      const double sinc = m == 0 ? 1.0 : std::sin(x) / x;
+      d[i] = i == n / 2 ? (R)0 : (R)(1.0 / (sinc * sinc));
+    }
+    gg_status st = upload(plan, &plan->tab.cic_deconv, d);
+    if (st != GG_OK) return st;
+  }
+  gg_status st = forward_zy<R>(plan, 0, in);
+  if (st != GG_OK) return st;
+  gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
+  x.fwd = 1;
+  x.inv = 0;
+  x.nout = 1;
+  x.dst[0] = plan->work;
+  x.mul[0] = gg::kMulNone;
+  x.variant = plan->variant[1];
+  if ((st = launch_axis_timed<R>(plan, x, kXFused, "x forward pass")) != GG_OK) return st;
+  gg::SpecScaleArgs sc{};
+  sc.spec = plan->work;
+  sc.n = n;
+  sc.qmax = top_hat_qmax(plan->p.box, r_s);
+  sc.axis_factor = plan->tab.cic_deconv;
+  sc.scale = 1.0 / ((double)n * n * n);
+  cudaError_t e = gg::launch_spectrum_scale<R>(sc, plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "spectrum scale");
+  x.fwd = 0;
+  x.inv = 1;
+  x.variant = plan->variant[3];
+  if ((st = launch_axis_timed<R>(plan, x, kYInvX, "x inverse pass")) != GG_OK) return st;
+  gg::AxisArgs y = axis_args<R>(plan, 1, plan->work);
+  y.inv = 1;
+  y.nout = 1;
+  y.dst[0] = plan->work;
+  y.mul[0] = gg::kMulNone;
+  y.variant = plan->variant[3];
+  if ((st = launch_axis_timed<R>(plan, y, kYInvX, "y inverse pass")) != GG_OK) return st;
+  return zinv_pass<R>(plan, 0, plan->work, out, nullptr, nullptr, false);
 }
 
 gg::CicArgs cic_args(const gg_plan_t *plan, const void *const psi[3]) {
@@ -1150,6 +1215,42 @@ gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
   }
   return plan->real_bytes == 8 ? run_zeldovich<double>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev)
                                : run_zeldovich<float>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev);
+}
+
+gg_status gg_large_scales(gg_plan_t *plan, double r_s, const void *in_dev, void *out_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!(r_s > 0) || !std::isfinite(r_s)) return fail(plan, GG_EINVAL, "r_s must be > 0");
+  if (!in_dev || !out_dev || !aligned16(in_dev) || !aligned16(out_dev))
+    return fail(plan, GG_EINVAL, "in/out NULL or unaligned");
+  return plan->real_bytes == 8 ? run_large_scales<double>(plan, r_s, in_dev, out_dev)
+                               : run_large_scales<float>(plan, r_s, in_dev, out_dev);
+}
+
+gg_status gg_zeldovich_merge(gg_plan_t *plan, uint64_t seed, const void *noise_dev, double r_s,
+                             int64_t n_low, const void *const large_dev[3], void *const psi_dev[3],
+                             void *const pos_dev[3], void *const vel_dev[3]) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!(r_s > 0) || !std::isfinite(r_s)) return fail(plan, GG_EINVAL, "r_s must be > 0");
+  if (n_low < 1 || n_low > plan->p.n) return fail(plan, GG_EINVAL, "n_low must be in [1, n]");
+  if (noise_dev && !aligned16(noise_dev)) return fail(plan, GG_EINVAL, "noise_dev unaligned");
+  for (int j = 0; j < 3; ++j) {
+    const void *bufs[4] = {large_dev ? large_dev[j] : nullptr, psi_dev ? psi_dev[j] : nullptr,
+                           pos_dev ? pos_dev[j] : nullptr, vel_dev ? vel_dev[j] : nullptr};
+    for (const void *b : bufs)
+      if (b && !aligned16(b)) return fail(plan, GG_EINVAL, "buffer unaligned");
+  }
+  const int64_t qmax_all = 3 * (plan->p.n / 2) * (plan->p.n / 2) + 1;
+  const int64_t q = top_hat_qmax(plan->p.box, r_s);
+  plan->merge_qmin = (int)(q < qmax_all ? q : qmax_all);
+  plan->merge_nlow = (int)n_low;
+  for (int j = 0; j < 3; ++j) plan->merge_large[j] = large_dev ? large_dev[j] : nullptr;
+  const gg_status st =
+      plan->real_bytes == 8 ? run_zeldovich<double>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev)
+                            : run_zeldovich<float>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev);
+  plan->merge_qmin = 0;
+  plan->merge_nlow = 0;
+  for (int j = 0; j < 3; ++j) plan->merge_large[j] = nullptr;
+  return st;
 }
 
 gg_status gg_zeldovich_adjoint(gg_plan_t *plan, const void *const g_psi_dev[3], void *g_noise_dev) {

@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
             f = (R)((2.f * t3 - 3.f * t2 + 1.f) * cc.x + (t3 - 2.f * t2 + t) * cc.y +
                     (3.f * t2 - 2.f * t3) * cc.z + (t3 - t2) * cc.w);
           }
+          if (q < a.qmin) f = (R)0;  // Eq. 4: large scales removed
           X[b * RH + r] = C{f * X[b * RH + r].x, f * X[b * RH + r].y};
         }
     }
@@ -280,12 +281,22 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
     C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
     C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
+    const R *large = reinterpret_cast<const R *>(a.large);
+    CicAxis<R> cx{}, cy{};
+    if (large) {
+      cx = cic_axis<R>((int)ix, a.n_low, N);
+      cy = cic_axis<R>((int)iy, a.n_low, N);
+    }
 #pragma unroll
     for (int b = 0; b < NBL; ++b)
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
         const int n = p + P * b + r * SPANL;
-        const C z = v[b * RL + r];
+        C z = v[b * RL + r];
+        if (large) {  // Sec. 2.4: the interpolated coarse large scales
+          z.x += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n, a.n_low, N));
+          z.y += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n + 1, a.n_low, N));
+        }
         if (psi) {
           if (a.accumulate) {
             const C o = psi[n];

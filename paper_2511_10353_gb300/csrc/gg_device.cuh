@@ -112,6 +112,40 @@ __device__ __forceinline__ R wrap_box(R x, R box) {
   return x;
 }
 
+// Cloud-in-cell (trilinear) interpolation between the cell centres of a
+// periodic coarse grid of nl points per axis, evaluated at the centre of
+// fine cell i of a grid of nh points: in coarse cell-centre units the centre
+// is u = (i + 1/2) nl / nh - 1/2 = ((2i + 1) nl - nh) / (2 nh), taken as an
+// exact fraction (floor by integer division, weight of the upper cell t).
+template <typename R> struct CicAxis {
+  int i0, i1;
+  R t;
+};
+template <typename R> __device__ __forceinline__ CicAxis<R> cic_axis(int i, int nl, int nh) {
+  const int num = (2 * i + 1) * nl - nh, den = 2 * nh;
+  const int q = num >= 0 ? num / den : -((den - 1 - num) / den);  // floor(num / den) >= -1
+  CicAxis<R> c;
+  c.t = (R)(num - q * den) / (R)den;
+  c.i0 = q < 0 ? q + nl : q;
+  c.i1 = c.i0 + 1 == nl ? 0 : c.i0 + 1;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ R cic_sample(const R *__restrict__ g, int nl, const CicAxis<R> &x,
+                                        const CicAxis<R> &y, const CicAxis<R> &z) {
+  auto at = [&](int a, int b, int c) { return __ldg(g + ((int64_t)a * nl + b) * nl + c); };
+  const R wx[2] = {(R)1 - x.t, x.t}, wy[2] = {(R)1 - y.t, y.t}, wz[2] = {(R)1 - z.t, z.t};
+  const int ix[2] = {x.i0, x.i1}, iy[2] = {y.i0, y.i1}, iz[2] = {z.i0, z.i1};
+  R s = (R)0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) s += at(ix[a], iy[b], iz[c]) * wx[a] * wy[b] * wz[c];
+  return s;
+}
+
 // ------------------------------------------------------------------ butterflies
 // In-register DFT of length RAD: y_k = sum_n x_n exp(-+2 pi i n k / RAD)
 // (minus sign forward, plus sign for INV).

@@ -77,6 +77,7 @@ struct AxisArgs {
   int variant;            // tile variant of the size-specialised kernel
   int nbatch;             // realizations in the buffers (<= 0 means 1), outermost
   int64_t batch_stride;   // complex elements between realizations
+  int qmin;               // with pre: modes with m2 < qmin get 0 (Eq. 4 top hat; 0: none)
 };
 
 // Forward z pass: real lines of N (generated noise or caller noise) -> half
@@ -123,6 +124,11 @@ struct ZInvArgs {
   void *const *psi_list;  // batched form: device arrays of per-realization outputs
   void *const *pos_list;  // (entries may be null); when set they replace psi/pos/vel
   void *const *vel_list;
+  // Sec. 2.4 merge: a coarse periodic grid of n_low^3 reals (cell-centred)
+  // whose cloud-in-cell interpolation to this grid's cell centres is added to
+  // the transform's output before the epilogue; nullptr: none
+  const void *large;
+  int n_low;
 };
 
 // Cloud-in-cell density of the Zel'dovich particles and its adjoint. Particle
@@ -140,6 +146,16 @@ struct CicArgs {
 };
 template <typename R> cudaError_t launch_cic_deposit(const CicArgs &a, cudaStream_t s);
 template <typename R> cudaError_t launch_cic_adjoint(const CicArgs &a, cudaStream_t s);
+
+// Eq. 5 with the cloud-in-cell deconvolution on a half spectrum (gg_merge.cu).
+struct SpecScaleArgs {
+  void *spec;               // N x N x N/2 complex, in place
+  int n;
+  int64_t qmax;             // modes with m2 >= qmax become 0
+  const void *axis_factor;  // N reals: 1 / sinc^2(pi m_i / N) per array index (0 at N/2)
+  double scale;             // 1 / N^3 (unnormalised forward and inverse transforms)
+};
+template <typename R> cudaError_t launch_spectrum_scale(const SpecScaleArgs &a, cudaStream_t s);
 
 struct NoiseArgs {
   void *out;              // N^3 reals

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
 #pragma unroll
           for (int r = 0; r < RH; ++r) {
             const int q = tab_index(p + P * b + r * span);
-            const R f = q >= 0 ? __ldg(table + q) : (R)0;
+            const R f = (q >= 0 && q >= a.qmin) ? __ldg(table + q) : (R)0;  // qmin: Eq. 4
             V[b * RH + r] = Cx<R>{f * V[b * RH + r].x, f * V[b * RH + r].y};
           }
       }
@@ -357,10 +357,20 @@ __global__ void k_zinv(const ZInvArgs a) {
   C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
   C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
   C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
+  const R *large = reinterpret_cast<const R *>(a.large);
+  CicAxis<R> cx{}, cy{};
+  if (large) {
+    cx = cic_axis<R>((int)ix, a.n_low, a.n);
+    cy = cic_axis<R>((int)iy, a.n_low, a.n);
+  }
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const int n = p + P * i;
-    const C v = buf[lay(l, n)];
+    C v = buf[lay(l, n)];
+    if (large) {  // Sec. 2.4: the interpolated coarse large scales
+      v.x += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n, a.n_low, a.n));
+      v.y += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n + 1, a.n_low, a.n));
+    }
     if (psi) {
       if (a.accumulate) {
         const C o = psi[n];

@@ -116,6 +116,9 @@ def test_null_arguments_rejected():
     assert L.gg_zeldovich(None, 1, None, None, None, None) == gg.GG_EINVAL
     assert L.gg_sync(None) == gg.GG_EINVAL
     assert L.gg_noise_bits(1, -1, 4, None, None) == gg.GG_EINVAL
+    assert L.gg_large_scales(None, 1.0, None, None) == gg.GG_EINVAL
+    null3 = gg._VP3(None, None, None)
+    assert L.gg_zeldovich_merge(None, 1, None, 1.0, 8, null3, null3, null3, null3) == gg.GG_EINVAL
     L.gg_free(None)
 
 
