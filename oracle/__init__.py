@@ -21,6 +21,8 @@ computes (Ginnungagap, arXiv:2511.10353):
 * ``adjoint``   The transpose of the linear map W -> psi and of the CIC /
                 smoothing chain used for gradient checks.
 * ``refine``    Appendix A white-noise refinement (Eqs. A.1-A.28).
+* ``stats``     Sec. 2.1 diagnostics: shell-averaged power spectrum and
+                moments of a field.
 * ``merge``     Sec. 2.4: large scales of a coarse field (Eq. 5, with the
                 cloud-in-cell deconvolution and interpolation) plus small
                 scales of a fine one (Eq. 4), then Eq. 3.
