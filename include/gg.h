@@ -302,6 +302,24 @@ gg_status gg_cic_density(gg_plan_t *plan, const void *const psi_dev[3], void *de
 gg_status gg_cic_density_adjoint(gg_plan_t *plan, const void *const psi_dev[3],
                                  const void *g_delta_dev, void *const g_psi_dev[3]);
 
+/* ---------------------------------------------------------------- diagnostics
+ * Sec. 2.1: statistics of the white noise and the fields, and the power
+ * spectrum measured from a field. Both calls are synchronous (they return
+ * after the result is on the host) and use the plan's stream. */
+
+/* P(b) = (V / N^6) <|F(k)|^2> over the modes of shell b = floor(|m| + 1/2),
+ * b = 0 .. nbins - 1, F the unnormalised DFT of field_dev (N^3 reals of the
+ * plan's type, 16-byte aligned); k_out[b] = mean |k| of the shell's modes
+ * (h/Mpc), count_out[b] = modes of the full spectrum in the shell; modes
+ * with any |m_j| = N/2 are left out. 1 <= nbins <= N/2; any output may be
+ * NULL. Overwrites the plan's workspace. */
+gg_status gg_power_spectrum(gg_plan_t *plan, const void *field_dev, int nbins, double *k_out,
+                            double *p_out, int64_t *count_out);
+
+/* out = {mean, variance (population), minimum, maximum} of field_dev (N^3
+ * reals of the plan's type), accumulated in FP64. */
+gg_status gg_field_moments(gg_plan_t *plan, const void *field_dev, double out[4]);
+
 /* ------------------------------------------------------- large/small-scale merge
  * Sec. 2.4, Eqs. 4-5: the velocity field of a refined (high-resolution)
  * white noise takes its small scales from the fine grid and its large scales

@@ -116,6 +116,9 @@ _SIGS = {
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "gg_power_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_field_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_large_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "gg_zeldovich_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -357,6 +360,24 @@ class Plan:
         _check(lib().gg_zeldovich(self._h, ctypes.c_uint64(int(seed)),
                                   _dev_ptr(noise, self.dtype, self._cells()), *arrs), self._h)
         return out
+
+    def power_spectrum(self, field, nbins=None):
+        """Shell-averaged power spectrum of a field: (k, P, count) numpy arrays."""
+        import numpy as np
+        nb = self.n // 2 if nbins is None else int(nbins)
+        k, p, c = np.zeros(nb), np.zeros(nb), np.zeros(nb, dtype=np.int64)
+        self._bind_stream()
+        _check(lib().gg_power_spectrum(self._h, _dev_ptr(field, self.dtype, self._cells()), nb,
+                                       k.ctypes.data, p.ctypes.data, c.ctypes.data), self._h)
+        return k, p, c
+
+    def moments(self, field):
+        """(mean, variance, min, max) of a field, FP64."""
+        out = (ctypes.c_double * 4)()
+        self._bind_stream()
+        _check(lib().gg_field_moments(self._h, _dev_ptr(field, self.dtype, self._cells()), out),
+               self._h)
+        return tuple(out)
 
     def large_scales(self, field, r_s, out=None):
         """Sec. 2.4, Eq. 5 with the cloud-in-cell deconvolution of a real field."""

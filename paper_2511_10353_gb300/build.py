@@ -33,6 +33,7 @@ SOURCES = [
     "gg_cic.cu",
     "gg_refine.cu",
     "gg_merge.cu",
+    "gg_stats.cu",
     "gg_api.cpp",
     "gg_cosmo.cpp",
 ]

@@ -886,6 +886,91 @@ gg_status run_large_scales(gg_plan_t *plan, double r_s, const void *in, void *ou
   return zinv_pass<R>(plan, 0, plan->work, out, nullptr, nullptr, false);
 }
 
+template <typename R>
+gg_status run_power_spectrum(gg_plan_t *plan, const void *field, int nbins, double *k_out,
+                             double *p_out, int64_t *count_out) {
+  const int n = (int)plan->p.n;
+  gg_status st = forward_zy<R>(plan, 0, field);
+  if (st != GG_OK) return st;
+  gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
+  x.fwd = 1;
+  x.inv = 0;
+  x.nout = 1;
+  x.dst[0] = plan->work;
+  x.mul[0] = gg::kMulNone;
+  x.variant = plan->variant[1];
+  if ((st = launch_axis_timed<R>(plan, x, kXFused, "x forward pass")) != GG_OK) return st;
+  double *sums = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&sums, sizeof(double) * 3 * nbins, plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMallocAsync of the shell sums");
+  std::vector<double> h(3 * (size_t)nbins);
+  gg::ShellArgs a{};
+  a.spec = plan->work;
+  a.n = n;
+  a.nbins = nbins;
+  a.sums = sums;
+  if ((e = cudaMemsetAsync(sums, 0, sizeof(double) * 3 * nbins, plan->stream)) != cudaSuccess ||
+      (e = gg::launch_shell_sums<R>(a, plan->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h.data(), sums, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost,
+                           plan->stream)) != cudaSuccess ||
+      (e = cudaFreeAsync(sums, plan->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(plan->stream)) != cudaSuccess)
+    return cuda_fail(plan, e, "power spectrum shell sums");
+  const double box = plan->p.box, vol = box * box * box, n6 = std::pow((double)n, 6.0);
+  for (int b = 0; b < nbins; ++b) {
+    const double c = h[b];
+    if (count_out) count_out[b] = (int64_t)(c + 0.5);
+    if (p_out) p_out[b] = c > 0 ? vol / n6 * h[nbins + b] / c : 0.0;
+    if (k_out) k_out[b] = c > 0 ? 2.0 * kPi / box * h[2 * nbins + b] / c : 0.0;
+  }
+  return GG_OK;
+}
+
+template <typename R>
+gg_status run_moments(gg_plan_t *plan, const void *field, double out[4]) {
+  const int64_t count = plan->cells;
+  const int blocks = gg::moment_blocks<R>(count);
+  double *slots = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&slots, sizeof(double) * 3 * blocks, plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMallocAsync of the moment slots");
+  std::vector<double> h(3 * (size_t)blocks);
+  double mean = 0.0, var = 0.0, lo = 0.0, hi = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    gg::MomentArgs a{};
+    a.field = field;
+    a.count = count;
+    a.second = pass;
+    a.mean = mean;
+    a.slots = slots;
+    if ((e = gg::launch_moments<R>(a, blocks, plan->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h.data(), slots, sizeof(double) * 3 * blocks, cudaMemcpyDeviceToHost,
+                             plan->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(plan->stream)) != cudaSuccess)
+      break;
+    double s = 0.0;
+    for (int b = 0; b < blocks; ++b) s += h[3 * b];
+    if (pass == 0) {
+      mean = s / (double)count;
+      lo = h[1];
+      hi = h[2];
+      for (int b = 1; b < blocks; ++b) {
+        lo = std::min(lo, h[3 * b + 1]);
+        hi = std::max(hi, h[3 * b + 2]);
+      }
+    } else {
+      var = s / (double)count;
+    }
+  }
+  const cudaError_t ef = cudaFreeAsync(slots, plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "field moments");
+  if (ef != cudaSuccess) return cuda_fail(plan, ef, "field moments");
+  out[0] = mean;
+  out[1] = var;
+  out[2] = lo;
+  out[3] = hi;
+  return GG_OK;
+}
+
 gg::CicArgs cic_args(const gg_plan_t *plan, const void *const psi[3]) {
   gg::CicArgs a{};
   for (int j = 0; j < 3; ++j) a.psi[j] = psi[j];
@@ -1215,6 +1300,22 @@ gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
   }
   return plan->real_bytes == 8 ? run_zeldovich<double>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev)
                                : run_zeldovich<float>(plan, seed, noise_dev, psi_dev, pos_dev, vel_dev);
+}
+
+gg_status gg_power_spectrum(gg_plan_t *plan, const void *field_dev, int nbins, double *k_out,
+                            double *p_out, int64_t *count_out) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!field_dev || !aligned16(field_dev)) return fail(plan, GG_EINVAL, "field_dev NULL or unaligned");
+  if (nbins < 1 || nbins > plan->p.n / 2) return fail(plan, GG_EINVAL, "nbins must be in [1, N/2]");
+  return plan->real_bytes == 8 ? run_power_spectrum<double>(plan, field_dev, nbins, k_out, p_out, count_out)
+                               : run_power_spectrum<float>(plan, field_dev, nbins, k_out, p_out, count_out);
+}
+
+gg_status gg_field_moments(gg_plan_t *plan, const void *field_dev, double out[4]) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!field_dev || !out) return fail(plan, GG_EINVAL, "field_dev and out are required");
+  return plan->real_bytes == 8 ? run_moments<double>(plan, field_dev, out)
+                               : run_moments<float>(plan, field_dev, out);
 }
 
 gg_status gg_large_scales(gg_plan_t *plan, double r_s, const void *in_dev, void *out_dev) {

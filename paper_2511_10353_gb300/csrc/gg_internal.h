@@ -157,6 +157,24 @@ struct SpecScaleArgs {
 };
 template <typename R> cudaError_t launch_spectrum_scale(const SpecScaleArgs &a, cudaStream_t s);
 
+// Sec. 2.1 diagnostics (gg_stats.cu).
+struct ShellArgs {
+  const void *spec;  // N x N x N/2 complex (unnormalised forward transform)
+  int n;
+  int nbins;         // shells 0 .. nbins - 1 (nbins <= N / 2)
+  double *sums;      // device [3][nbins], added to: weight, weight |F|^2, weight |m|
+};
+template <typename R> cudaError_t launch_shell_sums(const ShellArgs &a, cudaStream_t s);
+struct MomentArgs {
+  const void *field;
+  int64_t count;
+  int second;        // 0: sum of values; 1: sum of squared deviations from mean
+  double mean;
+  double *slots;     // device [3 per CTA]: sum, min, max
+};
+template <typename R> int moment_blocks(int64_t count);
+template <typename R> cudaError_t launch_moments(const MomentArgs &a, int blocks, cudaStream_t s);
+
 struct NoiseArgs {
   void *out;              // N^3 reals
   uint64_t seed;
