@@ -21,6 +21,8 @@ computes (Ginnungagap, arXiv:2511.10353):
 * ``adjoint``   The transpose of the linear map W -> psi and of the CIC /
                 smoothing chain used for gradient checks.
 * ``refine``    Appendix A white-noise refinement (Eqs. A.1-A.28).
+* ``particles`` Sec. 2.2 particle-set options (periodic shift, gas pairs,
+                coordinate IDs) and the Sec. 2.4 degraded field.
 * ``stats``     Sec. 2.1 diagnostics: shell-averaged power spectrum and
                 moments of a field.
 * ``merge``     Sec. 2.4: large scales of a coarse field (Eq. 5, with the
