@@ -302,6 +302,41 @@ gg_status gg_cic_density(gg_plan_t *plan, const void *const psi_dev[3], void *de
 gg_status gg_cic_density_adjoint(gg_plan_t *plan, const void *const psi_dev[3],
                                  const void *g_delta_dev, void *const g_psi_dev[3]);
 
+/* ------------------------------------------------------------ particle options
+ * Sec. 2.2 (particle generation) and Sec. 2.4 (degrading). */
+
+/* Periodic shift (Mpc/h) added to every position the plan writes from now
+ * on: x = (q + shift + psi) mod L (e.g. to put a zoom region at the box
+ * centre). {0, 0, 0} turns it off. */
+gg_status gg_set_shift(gg_plan_t *plan, const double shift[3]);
+
+/* gg_zeldovich with gas partners: each dark-matter particle gets a gas
+ * particle half a cell away along every axis, and both move so that the
+ * pair's centre of mass stays at the particle: dark matter at
+ * x - f d, gas at x + (1 - f) d, d = (L / 2N)(1, 1, 1), f = gas_fraction
+ * (the gas mass fraction Omega_b / Omega_m, in [0, 1)); velocities (and psi)
+ * are shared. pos_dm_dev[j] and pos_gas_dev[j] are given (or NULL) together.
+ * Other arguments as gg_zeldovich. */
+gg_status gg_zeldovich_gas(gg_plan_t *plan, uint64_t seed, const void *noise_dev, double gas_fraction,
+                           void *const psi_dev[3], void *const pos_dm_dev[3],
+                           void *const pos_gas_dev[3], void *const vel_dev[3]);
+
+/* Coordinate-based particle IDs: ids_dev[(i N + j) N + k] (int64, N^3,
+ * caller-owned device memory) = offset + (I n_finest + J) n_finest + K,
+ * (I, J, K) = r (i, j, k) + floor(r / 2), r = n_finest / N: the cell of the
+ * simulation's finest grid (n_finest points per axis, a multiple of N) that
+ * holds the particle's Lagrangian position, so the ID gives that position
+ * back at every zoom level. */
+gg_status gg_particle_ids(gg_plan_t *plan, int64_t n_finest, int64_t offset, int64_t *ids_dev);
+
+/* Sec. 2.4: degrade a field of n_high^3 points (n_high = r N) to the plan's
+ * grid: coarse cell i takes the fine value at index r i (nearest grid
+ * point), and the coarse field is moved in Fourier space by (r - 1) / (2 r)
+ * cells along each axis so that the values sit at the coarse cell centres
+ * (modes with any |m_j| = N/2 dropped). high_dev: n_high^3 reals, low_dev:
+ * N^3 reals of the plan's type, 16-byte aligned. */
+gg_status gg_degrade(gg_plan_t *plan, int64_t n_high, const void *high_dev, void *low_dev);
+
 /* ---------------------------------------------------------------- diagnostics
  * Sec. 2.1: statistics of the white noise and the fields, and the power
  * spectrum measured from a field. Both calls are synchronous (they return

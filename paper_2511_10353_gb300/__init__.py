@@ -116,6 +116,13 @@ _SIGS = {
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "gg_set_shift": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_zeldovich_gas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_particle_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p]),
+    "gg_degrade": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_power_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_field_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -359,6 +366,46 @@ class Plan:
         self._bind_stream()
         _check(lib().gg_zeldovich(self._h, ctypes.c_uint64(int(seed)),
                                   _dev_ptr(noise, self.dtype, self._cells()), *arrs), self._h)
+        return out
+
+    def set_shift(self, shift):
+        """Periodic shift (Mpc/h) of every later position output."""
+        arr = (ctypes.c_double * 3)(*[float(v) for v in shift])
+        _check(lib().gg_set_shift(self._h, arr), self._h)
+
+    def zeldovich_gas(self, gas_fraction, seed=0, noise=None, psi=False, vel=True, out=None):
+        """Dark-matter and gas-partner positions (Sec. 2.2); returns
+        {"psi", "pos", "pos_gas", "vel"}."""
+        if out is None:
+            out = {"psi": [self.empty() for _ in range(3)] if psi else [None] * 3,
+                   "pos": [self.empty() for _ in range(3)],
+                   "pos_gas": [self.empty() for _ in range(3)],
+                   "vel": [self.empty() for _ in range(3)] if vel else [None] * 3}
+        arrs = [_VP3(*[_dev_ptr(t, self.dtype, self._cells()) for t in out[k]])
+                for k in ("psi", "pos", "pos_gas", "vel")]
+        self._bind_stream()
+        _check(lib().gg_zeldovich_gas(self._h, ctypes.c_uint64(int(seed)),
+                                      _dev_ptr(noise, self.dtype, self._cells()),
+                                      float(gas_fraction), *arrs), self._h)
+        return out
+
+    def particle_ids(self, n_finest=None, offset=0, out=None):
+        """Coordinate-based int64 IDs of the N^3 particles (Sec. 2.2)."""
+        nf = self.n if n_finest is None else int(n_finest)
+        if out is None:
+            out = self.torch.empty((self.n,) * 3, dtype=self.torch.int64, device=self.device)
+        self._bind_stream()
+        _check(lib().gg_particle_ids(self._h, nf, int(offset),
+                                     _dev_ptr(out, self.torch.int64, self._cells())), self._h)
+        return out
+
+    def degrade(self, high, out=None):
+        """Sec. 2.4: a field of (r N)^3 points degraded to this plan's grid."""
+        nh = int(high.shape[0])
+        out = self.empty() if out is None else out
+        self._bind_stream()
+        _check(lib().gg_degrade(self._h, nh, _dev_ptr(high, self.dtype, nh ** 3),
+                                _dev_ptr(out, self.dtype, self._cells())), self._h)
         return out
 
     def power_spectrum(self, field, nbins=None):

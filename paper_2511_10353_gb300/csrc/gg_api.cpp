@@ -87,6 +87,13 @@ struct gg_plan {
   int merge_qmin = 0;
   const void *merge_large[3] = {nullptr, nullptr, nullptr};
   int merge_nlow = 0;
+  // Sec. 2.2 particle options: periodic shift of every position (gg_set_shift)
+  // and, for the duration of gg_zeldovich_gas, the gas partners' outputs
+  double shift[3] = {0.0, 0.0, 0.0};
+  double gas_fraction = 0.0;
+  void *gas_pos[3] = {nullptr, nullptr, nullptr};
+  void *phase = nullptr;  // degrading: N complex phases (gg_degrade)
+  int64_t phase_r = 0;
 };
 
 struct gg_batch {
@@ -340,7 +347,7 @@ void release(gg_plan_t *plan) {
                   plan->tab.tw_n,    plan->tab.tw_half,   plan->tab.s_delta,
                   plan->tab.u_phi,   plan->err,           plan->noise_stage,
                   plan->tab.smooth,  plan->tab.interp_u,  plan->tab.interp_s,
-                  plan->tab.interp_smooth, plan->tab.cic_deconv};
+                  plan->tab.interp_smooth, plan->tab.cic_deconv, plan->phase};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (auto &slot : plan->stage)
@@ -498,6 +505,13 @@ gg_status zinv_pass(gg_plan_t *plan, int comp, const void *src, void *psi, void 
   z.variant = plan->variant[5];
   z.large = plan->merge_large[comp];
   z.n_low = plan->merge_nlow;
+  {  // Sec. 2.2: shift, and the gas pairs' offsets of half a cell per axis
+    const double half_cell = 0.5 * plan->p.box / (double)n;
+    const bool gas = plan->gas_pos[comp] != nullptr;
+    z.shift = plan->shift[comp] - (gas ? plan->gas_fraction * half_cell : 0.0);
+    z.pos2 = plan->gas_pos[comp];
+    z.shift2 = gas ? plan->shift[comp] + (1.0 - plan->gas_fraction) * half_cell : 0.0;
+  }
   const double cb = (double)plan->cells * sizeof(R);
   const int outs = (psi ? 1 : 0) + (pos ? 1 : 0) + (vel ? 1 : 0);
   cudaError_t e;
@@ -971,6 +985,64 @@ gg_status run_moments(gg_plan_t *plan, const void *field, double out[4]) {
   return GG_OK;
 }
 
+// Sec. 2.4 degrading: every r-th fine value (nearest grid point) into out,
+// then moved by t = (r - 1) / (2 r) cells onto the coarse cell centres:
+// forward passes, the spectrum times exp(2 pi i t m_j / N) per axis (and
+// 1 / N^3), inverse passes.
+template <typename R>
+gg_status run_degrade(gg_plan_t *plan, int64_t n_high, const void *high, void *out) {
+  const int n = (int)plan->p.n;
+  const int r = (int)(n_high / n);
+  if (plan->phase_r != r) {
+    std::vector<R> ph(2 * (size_t)n);
+    const double t = (double)(r - 1) / (2.0 * r);
+    for (int i = 0; i < n; ++i) {
+      const int m = i < n / 2 ? i : i - n;
+      const double a = 2.0 * kPi * t * m / n;
+      ph[2 * i] = i == n / 2 ? (R)0 : (R)std::cos(a);
+      ph[2 * i + 1] = i == n / 2 ? (R)0 : (R)std::sin(a);
+    }
+    if (plan->phase) {
+      cudaFree(plan->phase);
+      plan->phase = nullptr;
+    }
+    gg_status st = upload(plan, &plan->phase, ph);
+    if (st != GG_OK) return st;
+    plan->phase_r = r;
+  }
+  cudaError_t e = gg::launch_subsample<R>(high, n_high, r, out, plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "subsample");
+  gg_status st = forward_zy<R>(plan, 0, out);
+  if (st != GG_OK) return st;
+  gg::AxisArgs x = axis_args<R>(plan, 0, plan->work);
+  x.fwd = 1;
+  x.inv = 0;
+  x.nout = 1;
+  x.dst[0] = plan->work;
+  x.mul[0] = gg::kMulNone;
+  x.variant = plan->variant[1];
+  if ((st = launch_axis_timed<R>(plan, x, kXFused, "x forward pass")) != GG_OK) return st;
+  gg::SpecPhaseArgs ph{};
+  ph.spec = plan->work;
+  ph.n = n;
+  ph.phase = plan->phase;
+  ph.scale = 1.0 / ((double)n * n * n);
+  if ((e = gg::launch_spectrum_phase<R>(ph, plan->stream)) != cudaSuccess)
+    return cuda_fail(plan, e, "spectrum phase");
+  x.fwd = 0;
+  x.inv = 1;
+  x.variant = plan->variant[3];
+  if ((st = launch_axis_timed<R>(plan, x, kYInvX, "x inverse pass")) != GG_OK) return st;
+  gg::AxisArgs y = axis_args<R>(plan, 1, plan->work);
+  y.inv = 1;
+  y.nout = 1;
+  y.dst[0] = plan->work;
+  y.mul[0] = gg::kMulNone;
+  y.variant = plan->variant[3];
+  if ((st = launch_axis_timed<R>(plan, y, kYInvX, "y inverse pass")) != GG_OK) return st;
+  return zinv_pass<R>(plan, 0, plan->work, out, nullptr, nullptr, false);
+}
+
 gg::CicArgs cic_args(const gg_plan_t *plan, const void *const psi[3]) {
   gg::CicArgs a{};
   for (int j = 0; j < 3; ++j) a.psi[j] = psi[j];
@@ -1316,6 +1388,65 @@ gg_status gg_field_moments(gg_plan_t *plan, const void *field_dev, double out[4]
   if (!field_dev || !out) return fail(plan, GG_EINVAL, "field_dev and out are required");
   return plan->real_bytes == 8 ? run_moments<double>(plan, field_dev, out)
                                : run_moments<float>(plan, field_dev, out);
+}
+
+gg_status gg_set_shift(gg_plan_t *plan, const double shift[3]) {
+  if (!plan || !shift) return fail(plan, GG_EINVAL, "plan and shift are required");
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(shift[j])) return fail(plan, GG_EINVAL, "shift must be finite");
+  for (int j = 0; j < 3; ++j) {  // reduced into [0, L): positions are periodic
+    double v = std::fmod(shift[j], plan->p.box);
+    plan->shift[j] = v < 0 ? v + plan->p.box : v;
+  }
+  return GG_OK;
+}
+
+gg_status gg_zeldovich_gas(gg_plan_t *plan, uint64_t seed, const void *noise_dev, double gas_fraction,
+                           void *const psi_dev[3], void *const pos_dm_dev[3],
+                           void *const pos_gas_dev[3], void *const vel_dev[3]) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (!(gas_fraction >= 0.0 && gas_fraction < 1.0))
+    return fail(plan, GG_EINVAL, "gas_fraction must be in [0, 1)");
+  if (!pos_dm_dev || !pos_gas_dev) return fail(plan, GG_EINVAL, "pos_dm_dev and pos_gas_dev are required");
+  if (noise_dev && !aligned16(noise_dev)) return fail(plan, GG_EINVAL, "noise_dev unaligned");
+  for (int j = 0; j < 3; ++j) {
+    if (!pos_dm_dev[j] != !pos_gas_dev[j])
+      return fail(plan, GG_EINVAL, "pos_dm_dev[j] and pos_gas_dev[j] must be given together");
+    const void *bufs[4] = {psi_dev ? psi_dev[j] : nullptr, pos_dm_dev[j], pos_gas_dev[j],
+                           vel_dev ? vel_dev[j] : nullptr};
+    for (const void *b : bufs)
+      if (b && !aligned16(b)) return fail(plan, GG_EINVAL, "buffer unaligned");
+  }
+  plan->gas_fraction = gas_fraction;
+  for (int j = 0; j < 3; ++j) plan->gas_pos[j] = pos_gas_dev[j];
+  const gg_status st =
+      plan->real_bytes == 8 ? run_zeldovich<double>(plan, seed, noise_dev, psi_dev, pos_dm_dev, vel_dev)
+                            : run_zeldovich<float>(plan, seed, noise_dev, psi_dev, pos_dm_dev, vel_dev);
+  plan->gas_fraction = 0.0;
+  for (int j = 0; j < 3; ++j) plan->gas_pos[j] = nullptr;
+  return st;
+}
+
+gg_status gg_particle_ids(gg_plan_t *plan, int64_t n_finest, int64_t offset, int64_t *ids_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  const int64_t n = plan->p.n;
+  if (n_finest < n || n_finest % n || n_finest > ((int64_t)1 << 20))
+    return fail(plan, GG_EINVAL, "n_finest must be a multiple of N (<= 2^20)");
+  if (offset < 0 || offset > INT64_MAX - n_finest * n_finest * n_finest)
+    return fail(plan, GG_EINVAL, "offset out of range");
+  if (!ids_dev || !aligned16(ids_dev)) return fail(plan, GG_EINVAL, "ids_dev NULL or unaligned");
+  const cudaError_t e = gg::launch_particle_ids(n, n_finest, offset, ids_dev, plan->stream);
+  return e == cudaSuccess ? GG_OK : cuda_fail(plan, e, "particle IDs");
+}
+
+gg_status gg_degrade(gg_plan_t *plan, int64_t n_high, const void *high_dev, void *low_dev) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (n_high < plan->p.n || n_high % plan->p.n || n_high > 8192)
+    return fail(plan, GG_EINVAL, "n_high must be a multiple of N (<= 8192)");
+  if (!high_dev || !low_dev || !aligned16(high_dev) || !aligned16(low_dev))
+    return fail(plan, GG_EINVAL, "high_dev / low_dev NULL or unaligned");
+  return plan->real_bytes == 8 ? run_degrade<double>(plan, n_high, high_dev, low_dev)
+                               : run_degrade<float>(plan, n_high, high_dev, low_dev);
 }
 
 gg_status gg_large_scales(gg_plan_t *plan, double r_s, const void *in_dev, void *out_dev) {

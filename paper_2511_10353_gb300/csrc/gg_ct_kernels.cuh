@@ -16,7 +16,7 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // persistent CTAs, TMA double buffering, forward stages in place in shared
 // memory, the spectrum handed to the inverse stages in registers, each
 // inverse's last stage storing straight to HBM.
-template <typename R, int N, int V>
+template <typename R, int N, int V, bool CUT = false>
 __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
     k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
   using C = Cx<R>;
@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
             f = (R)((2.f * t3 - 3.f * t2 + 1.f) * cc.x + (t3 - 2.f * t2 + t) * cc.y +
                     (3.f * t2 - 2.f * t3) * cc.z + (t3 - t2) * cc.w);
           }
-          if (q < a.qmin) f = (R)0;  // Eq. 4: large scales removed
+          if constexpr (CUT) {
+            if (q < a.qmin) f = (R)0;  // Eq. 4: large scales removed
+          }
           X[b * RH + r] = C{f * X[b * RH + r].x, f * X[b * RH + r].y};
         }
     }
@@ -204,7 +206,9 @@ template <int LD, int PAD> __device__ __forceinline__ int zpad(int l, int n) {
 // buffer is free and the copy of the CTA's next block starts; it lands while
 // the transform and the epilogue of the current block run. The last stage's
 // outputs (natural order) feed the epilogue from registers.
-template <typename R, int N, int V>
+// EXT: the Sec. 2.4 merge (large) and the Sec. 2.2 particle options (shift,
+// pos2), compiled only into the extended instantiation.
+template <typename R, int N, int V, bool EXT = false>
 __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_INV)
     k_zinv_ct(const ZInvArgs a) {
   using C = Cx<R>;
@@ -281,9 +285,11 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
     C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
     C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
-    const R *large = reinterpret_cast<const R *>(a.large);
+    const R *large = EXT ? reinterpret_cast<const R *>(a.large) : nullptr;
+    C *pos2 = EXT && a.pos2 ? reinterpret_cast<C *>(a.pos2) + off : nullptr;
+    const R sh1 = EXT ? (R)a.shift : (R)0, sh2 = EXT ? (R)a.shift2 : (R)0;
     CicAxis<R> cx{}, cy{};
-    if (large) {
+    if (EXT && large) {
       cx = cic_axis<R>((int)ix, a.n_low, N);
       cy = cic_axis<R>((int)iy, a.n_low, N);
     }
@@ -293,9 +299,11 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       for (int r = 0; r < RL; ++r) {
         const int n = p + P * b + r * SPANL;
         C z = v[b * RL + r];
-        if (large) {  // Sec. 2.4: the interpolated coarse large scales
-          z.x += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n, a.n_low, N));
-          z.y += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n + 1, a.n_low, N));
+        if constexpr (EXT) {  // Sec. 2.4: the interpolated coarse large scales
+          if (large) {
+            z.x += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n, a.n_low, N));
+            z.y += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n + 1, a.n_low, N));
+          }
         }
         if (psi) {
           if (a.accumulate) {
@@ -311,7 +319,12 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
             q0 = (q2p + (R)(2 * (n - p)) + qo) * cell;
             q1 = (q2p + (R)(2 * (n - p) + 1) + qo) * cell;
           }
-          pos[n] = C{wrap_box<R>(q0 + z.x, box), wrap_box<R>(q1 + z.y, box)};
+          if constexpr (EXT) {  // Sec. 2.2: periodic shift; gas partners
+            pos[n] = C{wrap_box<R>(q0 + sh1 + z.x, box), wrap_box<R>(q1 + sh1 + z.y, box)};
+            if (pos2) pos2[n] = C{wrap_box<R>(q0 + sh2 + z.x, box), wrap_box<R>(q1 + sh2 + z.y, box)};
+          } else {
+            pos[n] = C{wrap_box<R>(q0 + z.x, box), wrap_box<R>(q1 + z.y, box)};
+          }
         }
         if (vel) vel[n] = C{vfac * z.x, vfac * z.y};
       }
@@ -378,7 +391,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
 }
 
 // ------------------------------------------------------------ launchers
-template <typename R, int N, int V>
+template <typename R, int N, int V, bool CUT = false>
 cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   using Pol = ct::AxisPolicy<R, N, V>;
   AxisArgs a = in;
@@ -393,19 +406,19 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   const bool interp = sizeof(R) == 4 && a.pre && a.interp;
   const size_t smem = 128 + 2 * tile +
                       (interp ? kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16 : 0);
-  auto kern = k_axis_ct<R, N, V>;
+  auto kern = k_axis_ct<R, N, V, CUT>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, tiles), Pol::THREADS, smem, s>>>(map, a);
   return cudaGetLastError();
 }
 
-template <typename R, int N, int V>
+template <typename R, int N, int V, bool EXT = false>
 cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
   using Pol = ct::ZPolicy<R, N, V>;
   const size_t dense = (Pol::DENSE * 2 * sizeof(R) + 127) & ~(size_t)127;
   const size_t smem = 128 + dense + (size_t)Pol::WORK_INV * 2 * sizeof(R);
-  auto kern = k_zinv_ct<R, N, V>;
+  auto kern = k_zinv_ct<R, N, V, EXT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, a.nlines / Pol::L), Pol::THREADS, smem, s>>>(a);
@@ -439,6 +452,7 @@ template <typename R, int... NS> struct CtTable {
     return m;
   }
   template <int N> static cudaError_t axis_n(const AxisArgs &a, cudaStream_t s) {
+    if (a.pre && a.qmin > 0) return ct_launch_axis<R, N, 0, true>(a, s);  // the Sec. 2.4 cut: variant 0
     return a.variant == 1 ? ct_launch_axis<R, N, 1>(a, s)
                           : (a.variant == 2 ? ct_launch_axis<R, N, 2>(a, s) : ct_launch_axis<R, N, 0>(a, s));
   }
@@ -448,6 +462,8 @@ template <typename R, int... NS> struct CtTable {
     return e;
   }
   template <int N> static cudaError_t zinv_n(const ZInvArgs &a, cudaStream_t s) {
+    if (a.large || a.pos2 || a.shift != 0.0 || a.shift2 != 0.0)  // Secs. 2.2, 2.4 options: variant 0
+      return ct_launch_zinv<R, N, 0, true>(a, s);
     return a.variant == 1 ? ct_launch_zinv<R, N, 1>(a, s)
                           : (a.variant == 2 ? ct_launch_zinv<R, N, 2>(a, s) : ct_launch_zinv<R, N, 0>(a, s));
   }

@@ -129,6 +129,12 @@ struct ZInvArgs {
   // the transform's output before the epilogue; nullptr: none
   const void *large;
   int n_low;
+  // Sec. 2.2 particle options: shift added to q for pos (periodic shift, and
+  // the dark-matter offset of gas pairs); pos2: a second position output
+  // (the gas partners) with its own shift2; nullptr: none
+  double shift;
+  void *pos2;
+  double shift2;
 };
 
 // Cloud-in-cell density of the Zel'dovich particles and its adjoint. Particle
@@ -156,6 +162,21 @@ struct SpecScaleArgs {
   double scale;             // 1 / N^3 (unnormalised forward and inverse transforms)
 };
 template <typename R> cudaError_t launch_spectrum_scale(const SpecScaleArgs &a, cudaStream_t s);
+// Sec. 2.4 degrading: multiply a half spectrum by phase[x] phase[y] phase[k_z]
+// (complex, N entries, 0 at N/2) and scale.
+struct SpecPhaseArgs {
+  void *spec;
+  int n;
+  const void *phase;  // N complex of the spectrum's type
+  double scale;
+};
+template <typename R> cudaError_t launch_spectrum_phase(const SpecPhaseArgs &a, cudaStream_t s);
+// every r-th value of a fine n_high^3 grid into a coarse (n_high / r)^3 grid
+template <typename R>
+cudaError_t launch_subsample(const void *fine, int64_t n_high, int r, void *coarse, cudaStream_t s);
+// coordinate-based particle IDs (Sec. 2.2), int64 per cell of an N^3 grid
+cudaError_t launch_particle_ids(int64_t n, int64_t n_finest, int64_t offset, int64_t *ids,
+                                cudaStream_t s);
 
 // Sec. 2.1 diagnostics (gg_stats.cu).
 struct ShellArgs {

@@ -385,7 +385,11 @@ __global__ void k_zinv(const ZInvArgs a) {
         q0 = ((R)(2 * n) + qo) * cell;
         q1 = ((R)(2 * n + 1) + qo) * cell;
       }
-      pos[n] = C{wrap_box<R>(q0 + v.x, box), wrap_box<R>(q1 + v.y, box)};
+      const R sh1 = (R)a.shift, sh2 = (R)a.shift2;  // Sec. 2.2: periodic shift, gas partners
+      pos[n] = C{wrap_box<R>(q0 + sh1 + v.x, box), wrap_box<R>(q1 + sh1 + v.y, box)};
+      if (a.pos2)
+        reinterpret_cast<C *>(a.pos2)[off + n] =
+            C{wrap_box<R>(q0 + sh2 + v.x, box), wrap_box<R>(q1 + sh2 + v.y, box)};
     }
     if (vel) vel[n] = C{vfac * v.x, vfac * v.y};
   }

@@ -119,6 +119,12 @@ def test_null_arguments_rejected():
     assert L.gg_large_scales(None, 1.0, None, None) == gg.GG_EINVAL
     null3 = gg._VP3(None, None, None)
     assert L.gg_zeldovich_merge(None, 1, None, 1.0, 8, null3, null3, null3, null3) == gg.GG_EINVAL
+    assert L.gg_set_shift(None, None) == gg.GG_EINVAL
+    assert L.gg_zeldovich_gas(None, 1, None, 0.1, null3, null3, null3, null3) == gg.GG_EINVAL
+    assert L.gg_particle_ids(None, 16, 0, None) == gg.GG_EINVAL
+    assert L.gg_degrade(None, 32, None, None) == gg.GG_EINVAL
+    assert L.gg_power_spectrum(None, None, 4, None, None, None) == gg.GG_EINVAL
+    assert L.gg_field_moments(None, None, None) == gg.GG_EINVAL
     L.gg_free(None)
 
 
