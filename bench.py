@@ -342,6 +342,83 @@ def run_refine(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------- the operations beyond the path
+FEATURES_METRIC = "ms and algorithmic GB/s per call of the Sec. 2.1-2.4 operations at 512^3 FP32"
+
+
+def run_features(args):
+    """Times each operation around the main path once per step (CUDA events on
+    the current stream): the Sec. 2.4 large-scale filter (256^3) and merge
+    (512^3 with 256^3 large scales), gas pairs, degrading 512^3 -> 256^3, the
+    power spectrum, coordinate IDs and the Appendix A refinement 256^3 ->
+    512^3. Algorithmic bytes (FP32) per call are stated per operation."""
+    import torch
+    import paper_2511_10353_gb300 as gg
+    from paper_2511_10353_gb300 import build
+    from paper_2511_10353_gb300.workloads import BBKS
+    torch.cuda.set_device(0)
+    build.build(verbose=False)
+    n, nl, box, z = 512, 256, 500.0, 100.0
+    hi = gg.Plan(n, box, BBKS, z, "f32")
+    lo = gg.Plan(nl, box, BBKS, z, "f32")
+    hi.autotune(2)
+    lo.autotune(2)
+    r_s = 2 * box / nl
+    psi_lo = lo.zeldovich(seed=1, pos=False, vel=False)["psi"]
+    large = [lo.empty() for _ in range(3)]
+    out = hi.zeldovich(seed=2)
+    gas = [hi.empty() for _ in range(3)]
+    ids = torch.empty((n, n, n), dtype=torch.int64, device="cuda")
+    coarse = lo.empty()
+    delta = hi.gaussian_field(seed=3)
+    parent = lo.white_noise(seed=4)
+    child = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    c, cl = n ** 3, nl ** 3
+    ops = {
+        "large_scales_256": (lambda: [lo.large_scales(psi_lo[j], r_s, out=large[j]) for j in range(3)],
+                             3 * 56.0 * cl, "3 components, 56 B/cell: 7 passes"),
+        "zeldovich_merge_512": (lambda: hi.zeldovich_merge(large, r_s, seed=2, out=out),
+                                80.0 * c + 3 * 4.0 * cl, "80 B/cell + the 256^3 large scales"),
+        "zeldovich_gas_512": (lambda: hi.zeldovich_gas(0.163, seed=2, out={"psi": [None] * 3,
+                              "pos": out["pos"], "pos_gas": gas, "vel": out["vel"]}),
+                              92.0 * c, "80 B/cell + 3 gas position grids"),
+        "zeldovich_plain_512": (lambda: hi.zeldovich(seed=2, out=out), 80.0 * c, "the main path"),
+        "degrade_512_to_256": (lambda: lo.degrade(delta, out=coarse), 4.0 * cl + 56.0 * cl,
+                               "gather + 56 B/coarse cell"),
+        "power_spectrum_512": (lambda: hi.power_spectrum(delta), 28.0 * c, "3 forward passes + bins"),
+        "particle_ids_512": (lambda: hi.particle_ids(n, 0, out=ids), 8.0 * c, "int64 write"),
+        "refine_256_to_512": (lambda: gg.refine_noise(parent, 5, "2", out=child), 4.0 * (cl + c),
+                              "parent read + child write"),
+    }
+    peak, src = peak_hbm()
+    res = {}
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 20))
+    for name, (fn, nbytes, note) in ops.items():
+        for _ in range(max(2, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "GB_s": gbs, "frac_of_peak": gbs / peak, "bytes": nbytes, "bytes_note": note}
+    line = {"metric": FEATURES_METRIC, "value": res["zeldovich_merge_512"]["ms"], "unit": "ms",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "features_512", "n": n, "n_low": nl, "box_mpc_h": box,
+                       "peak_GB_s": peak, "peak_source": src},
+            "features": res}
+    for p in (hi, lo):
+        p.close()
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -350,6 +427,13 @@ def main():
         return
     if args.workload.startswith("refine_"):
         run_refine(args)
+        return
+    if args.workload == "features_512":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "features_512 has no oracle arm; "
+                              "the oracle is timed by the main workloads"}), flush=True)
+            return
+        run_features(args)
         return
     from paper_2511_10353_gb300.workloads import WORKLOADS
     w = dict(WORKLOADS[args.workload])

@@ -94,6 +94,9 @@ struct gg_plan {
   void *gas_pos[3] = {nullptr, nullptr, nullptr};
   void *phase = nullptr;  // degrading: N complex phases (gg_degrade)
   int64_t phase_r = 0;
+  // power spectrum: the grid's shell weights and weighted |m| for shell_nb shells
+  std::vector<double> shell_w, shell_m;
+  int shell_nb = 0;
 };
 
 struct gg_batch {
@@ -915,27 +918,41 @@ gg_status run_power_spectrum(gg_plan_t *plan, const void *field, int nbins, doub
   x.variant = plan->variant[1];
   if ((st = launch_axis_timed<R>(plan, x, kXFused, "x forward pass")) != GG_OK) return st;
   double *sums = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&sums, sizeof(double) * 3 * nbins, plan->stream);
+  cudaError_t e = cudaMallocAsync((void **)&sums, sizeof(double) * 2 * nbins, plan->stream);
   if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMallocAsync of the shell sums");
-  std::vector<double> h(3 * (size_t)nbins);
   gg::ShellArgs a{};
   a.spec = plan->work;
   a.n = n;
   a.nbins = nbins;
   a.sums = sums;
-  if ((e = cudaMemsetAsync(sums, 0, sizeof(double) * 3 * nbins, plan->stream)) != cudaSuccess ||
-      (e = gg::launch_shell_sums<R>(a, plan->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h.data(), sums, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost,
-                           plan->stream)) != cudaSuccess ||
-      (e = cudaFreeAsync(sums, plan->stream)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(plan->stream)) != cudaSuccess)
-    return cuda_fail(plan, e, "power spectrum shell sums");
+  auto pass = [&](bool geometry, std::vector<double> &h) {
+    h.assign((geometry ? 2 : 1) * (size_t)nbins, 0.0);
+    cudaError_t ee;
+    if ((ee = cudaMemsetAsync(sums, 0, sizeof(double) * h.size(), plan->stream)) != cudaSuccess ||
+        (ee = gg::launch_shell_sums<R>(a, geometry, plan->stream)) != cudaSuccess ||
+        (ee = cudaMemcpyAsync(h.data(), sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                              plan->stream)) != cudaSuccess)
+      return ee;
+    return cudaStreamSynchronize(plan->stream);
+  };
+  std::vector<double> geo, pw;
+  if (plan->shell_nb != nbins) {  // the grid's own sums, once per shell count
+    if ((e = pass(true, geo)) == cudaSuccess) {
+      plan->shell_w.assign(geo.begin(), geo.begin() + nbins);
+      plan->shell_m.assign(geo.begin() + nbins, geo.end());
+      plan->shell_nb = nbins;
+    }
+  }
+  if (e == cudaSuccess) e = pass(false, pw);
+  const cudaError_t ef = cudaFreeAsync(sums, plan->stream);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "power spectrum shell sums");
+  if (ef != cudaSuccess) return cuda_fail(plan, ef, "power spectrum shell sums");
   const double box = plan->p.box, vol = box * box * box, n6 = std::pow((double)n, 6.0);
   for (int b = 0; b < nbins; ++b) {
-    const double c = h[b];
+    const double c = plan->shell_w[b];
     if (count_out) count_out[b] = (int64_t)(c + 0.5);
-    if (p_out) p_out[b] = c > 0 ? vol / n6 * h[nbins + b] / c : 0.0;
-    if (k_out) k_out[b] = c > 0 ? 2.0 * kPi / box * h[2 * nbins + b] / c : 0.0;
+    if (p_out) p_out[b] = c > 0 ? vol / n6 * pw[b] / c : 0.0;
+    if (k_out) k_out[b] = c > 0 ? 2.0 * kPi / box * plan->shell_m[b] / c : 0.0;
   }
   return GG_OK;
 }

@@ -183,9 +183,10 @@ struct ShellArgs {
   const void *spec;  // N x N x N/2 complex (unnormalised forward transform)
   int n;
   int nbins;         // shells 0 .. nbins - 1 (nbins <= N / 2)
-  double *sums;      // device [3][nbins], added to: weight, weight |F|^2, weight |m|
+  double *sums;      // device, added to: geometry [2][nbins] weight, weight |m|;
+                     // otherwise [nbins] weight |F|^2
 };
-template <typename R> cudaError_t launch_shell_sums(const ShellArgs &a, cudaStream_t s);
+template <typename R> cudaError_t launch_shell_sums(const ShellArgs &a, bool geometry, cudaStream_t s);
 struct MomentArgs {
   const void *field;
   int64_t count;

@@ -72,14 +72,18 @@ __global__ void __launch_bounds__(256) k_subsample(const R *__restrict__ fine, i
   }
 }
 
-// ID = offset + (I n_f + J) n_f + K with (I, J, K) = r (i, j, k) + floor(r / 2)
+// ID = offset + (I n_f + J) n_f + K with (I, J, K) = r (i, j, k) + floor(r / 2);
+// one warp per z line (coalesced stores, no division in the inner loop)
 __global__ void __launch_bounds__(256) k_particle_ids(int64_t n, int64_t nf, int64_t offset,
                                                       int64_t *__restrict__ ids) {
-  const int64_t total = n * n * n, r = nf / n, h = r / 2;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = i % n, t = i / n, j = t % n, x = t / n;
-    ids[i] = offset + ((r * x + h) * nf + (r * j + h)) * nf + (r * k + h);
+  const int64_t r = nf / n, h = r / 2, lines = n * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wstep = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; line < lines; line += wstep) {
+    const int64_t j = line % n, x = line / n;
+    const int64_t base = offset + ((r * x + h) * nf + (r * j + h)) * nf + h;
+    int64_t *row = ids + line * n;
+    for (int64_t k = lane; k < n; k += 32) row[k] = base + r * k;
   }
 }
 
@@ -109,7 +113,7 @@ cudaError_t launch_subsample(const void *fine, int64_t n_high, int r, void *coar
 
 cudaError_t launch_particle_ids(int64_t n, int64_t n_finest, int64_t offset, int64_t *ids,
                                 cudaStream_t s) {
-  k_particle_ids<<<grid_of(n * n * n), 256, 0, s>>>(n, n_finest, offset, ids);
+  k_particle_ids<<<grid_of(n * n * 4), 256, 0, s>>>(n, n_finest, offset, ids);
   return cudaGetLastError();
 }
 
