@@ -241,7 +241,7 @@ def run_batched(args):
                        "l2": "working set > L2 (129 MB), no flush", "parallelism": "replicas"},
             "path": {"algorithmic_bytes_per_cell": 80.0, "GB_s": gbs, "frac_of_peak": gbs / peak,
                      "peak_source": src},
-            "gpu_launches": None, "clocks": clocks}
+            "gpu_launches": b.launches() * args.steps, "clocks": clocks}
     b.close()
     print(json.dumps(line), flush=True)
 

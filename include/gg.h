@@ -246,6 +246,10 @@ gg_status gg_batch_sync(gg_batch_t *batch);
 /* Number of groups and total cells of the batch. */
 gg_status gg_batch_info(const gg_batch_t *batch, int *groups, int64_t *cells);
 
+/* Kernels one gg_batch_run launches: the kernel nodes of the captured CUDA
+ * graph (0 before the first gg_batch_run). */
+gg_status gg_batch_launches(const gg_batch_t *batch, int *kernels);
+
 void gg_batch_free(gg_batch_t *batch);
 
 /* Largest grid (points per axis) that gg_gaussian_field_static accepts. */

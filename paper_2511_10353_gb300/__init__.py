@@ -111,6 +111,7 @@ _SIGS = {
     "gg_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int64)]),
     "gg_batch_free": (None, [ctypes.c_void_p]),
+    "gg_batch_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "gg_zeldovich_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_smooth": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -614,6 +615,12 @@ class Batch:
 
     def sync(self):
         _check(lib().gg_batch_sync(self._h))
+
+    def launches(self):
+        """Kernels one run launches (kernel nodes of the captured graph)."""
+        k = ctypes.c_int()
+        _check(lib().gg_batch_launches(self._h, ctypes.byref(k)))
+        return k.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1790,6 +1790,26 @@ gg_status gg_batch_info(const gg_batch_t *b, int *groups, int64_t *cells) {
   return GG_OK;
 }
 
+gg_status gg_batch_launches(const gg_batch_t *b, int *kernels) {
+  if (!b || !kernels) return fail(nullptr, GG_EINVAL, "batch and kernels are required");
+  *kernels = 0;
+  if (!b->graph) return GG_OK;  // not captured yet: no gg_batch_run so far
+  size_t count = 0;
+  cudaError_t e = cudaGraphGetNodes(b->graph, nullptr, &count);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGraphGetNodes");
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (count && (e = cudaGraphGetNodes(b->graph, nodes.data(), &count)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaGraphGetNodes");
+  int k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if ((e = cudaGraphNodeGetType(nd, &t)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaGraphNodeGetType");
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *kernels = k;
+  return GG_OK;
+}
+
 void gg_batch_free(gg_batch_t *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);

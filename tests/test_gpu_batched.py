@@ -50,6 +50,9 @@ def test_small_mixed_batch_equals_solo_runs(gg):
             for k in ("psi", "pos", "vel"):
                 for j in range(3):
                     assert np.array_equal(out[k][i][j].cpu().numpy(), want[k][j]), (i, k, j)
+    # one launch per pass and group: z forward, y forward, x, two y inverse
+    # passes (two-output passes may split), three z inverse passes
+    assert 8 * b.groups <= b.launches() <= 10 * b.groups
     b.close()
 
 
