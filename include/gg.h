@@ -170,10 +170,12 @@ gg_status gg_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise_dev,
                        void *const psi_dev[3], void *const pos_dev[3], void *const vel_dev[3]);
 
 /* gg_zeldovich with HOST buffers (pinned memory recommended): copies
- * noise_host (NULL = generate from seed) to the device, runs the path and
- * copies each requested output back, overlapping the copy of component j with
- * the compute of component j+1. Synchronous: returns when the outputs are in
- * host memory. */
+ * noise_host (NULL = generate from seed) to the device and runs the path.
+ * A component whose requested outputs are all pinned, mapped host memory is
+ * written there directly by the last pass (on a coherent CPU-GPU node, over
+ * the chip-to-chip link); otherwise each output goes through a device
+ * staging buffer and a copy that overlaps the compute of the next
+ * component. Synchronous: returns when the outputs are in host memory. */
 gg_status gg_zeldovich_host(gg_plan_t *plan, uint64_t seed, const void *noise_host,
                             void *const psi_host[3], void *const pos_host[3],
                             void *const vel_host[3]);

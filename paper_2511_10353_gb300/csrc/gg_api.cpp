@@ -673,6 +673,21 @@ gg_status create(gg_plan_t *plan, const gg::cosmo::Model &m) {
   return GG_OK;
 }
 
+// The device address of a host buffer the kernels can write directly
+// (pinned and mapped; on a coherent CPU-GPU node the stores then cross the
+// chip-to-chip link with no staging buffer and no copy engine); nullptr for
+// any other buffer.
+void *device_view(void *host) {
+  if (!host) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered pointer is not an error here
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer || !aligned16(at.devicePointer)) return nullptr;
+  return at.devicePointer;
+}
+
 template <typename R>
 gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void *const psi[3],
                    void *const pos[3], void *const vel[3]) {
@@ -710,6 +725,14 @@ gg_status run_host(gg_plan_t *plan, uint64_t seed, const void *noise_host, void 
   for (int j = 0; j < 3; ++j) {
     if (!want[j]) continue;
     void *hs[3] = {psi ? psi[j] : nullptr, pos ? pos[j] : nullptr, vel ? vel[j] : nullptr};
+    void *views[3] = {device_view(hs[0]), device_view(hs[1]), device_view(hs[2])};
+    if ((!hs[0] || views[0]) && (!hs[1] || views[1]) && (!hs[2] || views[2])) {
+      // every output of the component is device-addressable: the z inverse
+      // pass writes it in place
+      st = zinv_pass<R>(plan, j, src[j], views[0], views[1], views[2], j == 2);
+      if (st != GG_OK) return st;
+      continue;
+    }
     for (int o = 0; o < 3; ++o)
       if (hs[o] && !plan->stage[slot][o] && cudaMalloc(&plan->stage[slot][o], grid) != cudaSuccess)
         return fail(plan, GG_ENOMEM, "cudaMalloc of an output staging buffer failed");

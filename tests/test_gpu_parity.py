@@ -182,6 +182,13 @@ def test_host_buffer_entry_point(gg):
     h2 = plan.zeldovich_host(noise=grid, psi=True, pos=False, vel=False)
     d2 = plan.zeldovich(noise=grid.cuda(), pos=False, vel=False)
     assert np.array_equal(h2["psi"][1].numpy(), _np(d2["psi"][1]))
+    # pageable outputs take the staged path (device buffer + copy)
+    page = {k: [torch.empty((n, n, n), dtype=torch.float64) for _ in range(3)]
+            for k in ("psi", "pos", "vel")}
+    h3 = plan.zeldovich_host(seed=2, out=page)
+    for k in ("psi", "pos", "vel"):
+        for j in range(3):
+            assert np.array_equal(h3[k][j].numpy(), _np(dev[k][j]))
 
 
 def test_invalid_device_arguments(gg):
