@@ -599,9 +599,28 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             el = float(tt.item())
         esz = torch.finfo(dt).bits // 8
+        # the host link's own copy rates on the same pinned buffers: the step
+        # cannot beat h2d / rate_up + d2h / rate_down
+        dev = torch.empty(shape, dtype=dt, device="cuda")
+        rates = {}
+        for name, fn in (("d2h", lambda: hout["pos"][0].copy_(dev, non_blocking=True)),
+                         ("h2d", lambda: dev.copy_(hn, non_blocking=True))):
+            fn()
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record()
+            for _ in range(3):
+                fn()
+            c1.record()
+            torch.cuda.synchronize()
+            rates[name] = cells * esz * 3 / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        del dev
+        bound_s = cells * esz / (rates["h2d"] * 1e9) + 6 * cells * esz / (rates["d2h"] * 1e9)
         line["e2e"] = {"value": world * cells * ke / el, "unit": "cells/s", "steps": ke,
                        "h2d_bytes_per_step": cells * esz, "d2h_bytes_per_step": 6 * cells * esz,
-                       "api": "gg_zeldovich_host (pinned host noise in, pos/vel out)"}
+                       "api": "gg_zeldovich_host (pinned host noise in, pos/vel out)",
+                       "link_GB_s": rates, "frac_of_link_bound": bound_s / (el / ke)}
 
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
