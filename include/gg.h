@@ -209,7 +209,8 @@ gg_status gg_autotune(gg_plan_t *plan, int reps);
 gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]);
 
 /* Sets the tile variant per pass explicitly (same layout as gg_plan_variants;
- * values outside 0..2 are rejected). */
+ * the z passes [0] and [5] take 0..3, the strided passes 0..2; other values
+ * are rejected). */
 gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]);
 
 /* ---------------------------------------------------------------- batched form

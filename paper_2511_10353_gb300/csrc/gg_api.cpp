@@ -785,7 +785,8 @@ gg_status autotune(gg_plan_t *plan, int reps) {
   }
   const bool prof_was = plan->prof_on;
   void *vel[3] = {tmp, tmp, tmp};
-  for (int v = 0; v < 3; ++v) {
+  const int vmax = std::max(gg::kSpecZVariants, gg::kSpecAxisVariants);
+  for (int v = 0; v < vmax; ++v) {
     for (int i = 0; i < 6; ++i) plan->variant[i] = v < nvar[i] ? v : 0;
     plan->prof_on = false;
     if ((st = run_zeldovich<R>(plan, 1, nullptr, nullptr, nullptr, vel)) != GG_OK) break;  // warm
@@ -1627,8 +1628,10 @@ gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]) {
 
 gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]) {
   if (!plan || !v) return fail(plan, GG_EINVAL, "plan or v is NULL");
-  for (int i = 0; i < 6; ++i)
-    if (v[i] < 0 || v[i] > 2) return fail(plan, GG_EINVAL, "variant out of range");
+  for (int i = 0; i < 6; ++i) {  // passes 0 and 5 are z passes
+    const int nv = (i == 0 || i == 5) ? gg::kSpecZVariants : gg::kSpecAxisVariants;
+    if (v[i] < 0 || v[i] >= nv) return fail(plan, GG_EINVAL, "variant out of range");
+  }
   for (int i = 0; i < 6; ++i) plan->variant[i] = v[i];
   return GG_OK;
 }

@@ -213,7 +213,8 @@ template <typename R, int N, int V> struct AxisPolicy {
 // z passes: lines per tile, variant 0 ~256 threads (sized so that two dense
 // tiles and a padded tile fit in 160 KB), variant 1 half as many lines,
 // variant 2 the lines of variant 0 with warp instead of CTA barriers between
-// the stages (where each line lies within one warp; warps then drift apart).
+// the stages (where each line lies within one warp; warps then drift apart),
+// variant 3 the lines of variant 1 with warp barriers.
 template <typename R, int N, int V> struct ZPolicy {
   static constexpr int M = N / 2;
   static constexpr int E = elems(M);
@@ -235,14 +236,14 @@ template <typename R, int N, int V> struct ZPolicy {
   static constexpr int pick() {
     int l = 1;
     while (l < 64 && P * l * 2 <= 256 && (2 * (2 * l) * M + 2 * l * LD) * CB <= 160 * 1024) l *= 2;
-    if (V == 1 && l > 1) l /= 2;
+    if ((V == 1 || V == 3) && l > 1) l /= 2;
     return l;
   }
   static constexpr int L = pick();
   static constexpr int THREADS = P * L;
   // variant 2, and every line within one warp (P divides 32): the stages need
   // only warp barriers
-  static constexpr int SY = (V == 2 && P <= 32 && 32 % P == 0) ? kSyncWarp : kSyncCta;
+  static constexpr int SY = ((V == 2 || V == 3) && P <= 32 && 32 % P == 0) ? kSyncWarp : kSyncCta;
   static constexpr int DENSE = L * M;        // complex values of one dense tile
   static constexpr int WORK_INV = L * LD_INV;  // complex values of the padded tiles
   static constexpr int WORK_FWD = L * LD_FWD;

@@ -437,7 +437,7 @@ cudaError_t ct_launch_zfwd(const ZFwdArgs &a, cudaStream_t s) {
 }
 
 constexpr int kAxisVariants = 3;
-constexpr int kZVariants = 3;
+constexpr int kZVariants = 4;
 
 // Run-time dispatch over the specialised sizes and their tile variants.
 template <typename R, int... NS> struct CtTable {
@@ -464,12 +464,20 @@ template <typename R, int... NS> struct CtTable {
   template <int N> static cudaError_t zinv_n(const ZInvArgs &a, cudaStream_t s) {
     if (a.large || a.pos2 || a.shift != 0.0 || a.shift2 != 0.0)  // Secs. 2.2, 2.4 options: variant 0
       return ct_launch_zinv<R, N, 0, true>(a, s);
-    return a.variant == 1 ? ct_launch_zinv<R, N, 1>(a, s)
-                          : (a.variant == 2 ? ct_launch_zinv<R, N, 2>(a, s) : ct_launch_zinv<R, N, 0>(a, s));
+    switch (a.variant) {
+      case 1: return ct_launch_zinv<R, N, 1>(a, s);
+      case 2: return ct_launch_zinv<R, N, 2>(a, s);
+      case 3: return ct_launch_zinv<R, N, 3>(a, s);
+      default: return ct_launch_zinv<R, N, 0>(a, s);
+    }
   }
   template <int N> static cudaError_t zfwd_n(const ZFwdArgs &a, cudaStream_t s) {
-    return a.variant == 1 ? ct_launch_zfwd<R, N, 1>(a, s)
-                          : (a.variant == 2 ? ct_launch_zfwd<R, N, 2>(a, s) : ct_launch_zfwd<R, N, 0>(a, s));
+    switch (a.variant) {
+      case 1: return ct_launch_zfwd<R, N, 1>(a, s);
+      case 2: return ct_launch_zfwd<R, N, 2>(a, s);
+      case 3: return ct_launch_zfwd<R, N, 3>(a, s);
+      default: return ct_launch_zfwd<R, N, 0>(a, s);
+    }
   }
   static cudaError_t zinv(const ZInvArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;

@@ -214,7 +214,7 @@ template <typename R> int max_block_threads_axis(int e);
 template <typename R> bool spec_has(int n);
 template <typename R> int spec_axis_max_out(int n, int variant);
 constexpr int kSpecAxisVariants = 3;  // tile variants the autotuner times per strided pass
-constexpr int kSpecZVariants = 3;     // ... per z pass
+constexpr int kSpecZVariants = 4;     // ... per z pass
 template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zinv(const ZInvArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zfwd(const ZFwdArgs &a, cudaStream_t s);

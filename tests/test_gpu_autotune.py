@@ -34,8 +34,9 @@ def gg():
 def test_variants_bit_identical(gg, n, prec):
     plan = gg.Plan(n, float(n), BBKS, 50.0, prec)
     ref = None
-    for v in range(3):
-        plan.set_variants([v] * 6)
+    for v in range(4):
+        a = min(v, 2)  # the strided passes have three variants, the z passes four
+        plan.set_variants([v, a, a, a, a, v])
         out = plan.zeldovich(seed=7)
         plan.sync()
         got = [out[k][j].cpu().numpy() for k in ("psi", "pos", "vel") for j in range(3)]
@@ -50,7 +51,7 @@ def test_autotune_then_parity(gg):
     n = 128
     plan = gg.Plan(n, 128.0, BBKS, 50.0, "f32")
     v = plan.autotune(2)
-    assert len(v) == 6 and all(0 <= x <= 2 for x in v)
+    assert len(v) == 6 and all(0 <= x <= 2 for x in v[1:5]) and 0 <= v[0] <= 3 and 0 <= v[5] <= 3
     out = plan.zeldovich(seed=3)
     plan.sync()
     ora = run_oracle(dict(n=n, box=128.0, cosmo=BBKS, z_init=50.0), seed=3)
@@ -62,3 +63,5 @@ def test_set_variants_rejects_out_of_range(gg):
     plan = gg.Plan(32, 32.0, BBKS, 50.0, "f32")
     with pytest.raises(gg.GGError):
         plan.set_variants([0, 0, 3, 0, 0, 0])
+    with pytest.raises(gg.GGError):
+        plan.set_variants([4, 0, 0, 0, 0, 0])
