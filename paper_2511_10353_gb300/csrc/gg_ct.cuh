@@ -204,7 +204,13 @@ template <typename R, int N, int V> struct AxisPolicy {
   }
   static constexpr int B = pick();
   static constexpr int THREADS = P * B;
-  static constexpr int REG_BUDGET = 65536 / THREADS < 255 ? 65536 / THREADS : 255;
+  // variant 2 (small CTAs): register bound for two CTAs per SM where the
+  // shared memory (two tiles, FP32 filter table) lets two fit
+  static constexpr int SMEM_EST = 128 + 2 * N * B * CB +
+                                  (sizeof(R) == 4 ? 4096 + 16 * (N + N / 2 + 8) : 0);
+  static constexpr int MINB = (V == 2 && THREADS <= 256 && 2 * SMEM_EST <= 227 * 1024) ? 2 : 1;
+  static constexpr int REG_BUDGET =
+      65536 / (THREADS * MINB) < 255 ? 65536 / (THREADS * MINB) : 255;
   static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
   static constexpr int MAX_OUT = REG_NEED <= REG_BUDGET ? 2 : 1;
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));

@@ -17,7 +17,7 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // memory, the spectrum handed to the inverse stages in registers, each
 // inverse's last stage storing straight to HBM.
 template <typename R, int N, int V, bool CUT = false>
-__global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, 1)
+__global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
     k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
   using C = Cx<R>;
   using Pol = ct::AxisPolicy<R, N, V>;
