@@ -301,8 +301,10 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
         C z = v[b * RL + r];
         if constexpr (EXT) {  // Sec. 2.4: the interpolated coarse large scales
           if (large) {
-            z.x += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n, a.n_low, N));
-            z.y += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n + 1, a.n_low, N));
+            R l0, l1;
+            cic_pair<R>(large, a.n_low, N, cx, cy, n, l0, l1);
+            z.x += l0;
+            z.y += l1;
           }
         }
         if (psi) {

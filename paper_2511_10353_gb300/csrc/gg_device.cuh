@@ -130,20 +130,39 @@ template <typename R> __device__ __forceinline__ CicAxis<R> cic_axis(int i, int 
   c.i1 = c.i0 + 1 == nl ? 0 : c.i0 + 1;
   return c;
 }
+// Both fine cells 2n and 2n + 1 of a z line at once (nl <= nh): their
+// numerators differ by 2 nl < 2 nh, so one division serves both, and their
+// z taps lie in the three consecutive coarse cells q, q + 1, q + 2; each of
+// the four (x, y) coarse lines is read at those three points, combined
+// bilinearly in x and y, then linearly in z per cell.
 template <typename R>
-__device__ __forceinline__ R cic_sample(const R *__restrict__ g, int nl, const CicAxis<R> &x,
-                                        const CicAxis<R> &y, const CicAxis<R> &z) {
-  auto at = [&](int a, int b, int c) { return __ldg(g + ((int64_t)a * nl + b) * nl + c); };
-  const R wx[2] = {(R)1 - x.t, x.t}, wy[2] = {(R)1 - y.t, y.t}, wz[2] = {(R)1 - z.t, z.t};
-  const int ix[2] = {x.i0, x.i1}, iy[2] = {y.i0, y.i1}, iz[2] = {z.i0, z.i1};
-  R s = (R)0;
+__device__ __forceinline__ void cic_pair(const R *__restrict__ g, int nl, int nh, const CicAxis<R> &x,
+                                         const CicAxis<R> &y, int n, R &a0, R &a1) {
+  const int den = 2 * nh;
+  const int num0 = (4 * n + 1) * nl - nh;
+  const int q = num0 >= 0 ? num0 / den : -((den - 1 - num0) / den);  // floor, >= -1
+  const int r0 = num0 - q * den;
+  const int step = r0 + 2 * nl >= den ? 1 : 0;  // cell 2n + 1 starts one coarse cell later
+  const int r1 = r0 + 2 * nl - step * den;
+  const int z0 = q < 0 ? q + nl : q;
+  const int z1 = z0 + 1 == nl ? 0 : z0 + 1;
+  const int z2 = z1 + 1 == nl ? 0 : z1 + 1;
+  const R wx[2] = {(R)1 - x.t, x.t}, wy[2] = {(R)1 - y.t, y.t};
+  const int ix[2] = {x.i0, x.i1}, iy[2] = {y.i0, y.i1};
+  R c0 = (R)0, c1 = (R)0, c2 = (R)0;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) s += at(ix[a], iy[b], iz[c]) * wx[a] * wy[b] * wz[c];
-  return s;
+    for (int b = 0; b < 2; ++b) {
+      const R *line = g + ((int64_t)ix[a] * nl + iy[b]) * nl;
+      const R w = wx[a] * wy[b];
+      c0 += w * __ldg(line + z0);
+      c1 += w * __ldg(line + z1);
+      c2 += w * __ldg(line + z2);
+    }
+  const R t0 = (R)r0 / (R)den, t1 = (R)r1 / (R)den;
+  a0 = ((R)1 - t0) * c0 + t0 * c1;
+  a1 = step ? ((R)1 - t1) * c1 + t1 * c2 : ((R)1 - t1) * c0 + t1 * c1;
 }
 
 // ------------------------------------------------------------------ butterflies

@@ -368,8 +368,10 @@ __global__ void k_zinv(const ZInvArgs a) {
     const int n = p + P * i;
     C v = buf[lay(l, n)];
     if (large) {  // Sec. 2.4: the interpolated coarse large scales
-      v.x += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n, a.n_low, a.n));
-      v.y += cic_sample<R>(large, a.n_low, cx, cy, cic_axis<R>(2 * n + 1, a.n_low, a.n));
+      R l0, l1;
+      cic_pair<R>(large, a.n_low, a.n, cx, cy, n, l0, l1);
+      v.x += l0;
+      v.y += l1;
     }
     if (psi) {
       if (a.accumulate) {
