@@ -538,6 +538,8 @@ def main():
             "path": {"algorithmic_bytes_per_cell": step_bytes / cells, "GB_s": path_gbs,
                      "frac_of_peak": path_gbs / peak},
             "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
+    del out
+    torch.cuda.empty_cache()
 
     # FP64 plain path on the same workload, and the FP32 error against it
     if not args.no_fp64 and w["prec"] == "f32":
@@ -557,36 +559,55 @@ def main():
             errs.append(float(torch.linalg.vector_norm(psi32.double() - psi64)
                               / torch.linalg.vector_norm(psi64)))
         del psi64, psi32
-        out64 = {"psi": [None] * 3,
-                 "pos": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)],
-                 "vel": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)]}
-        plan64.zeldovich(seed=1, out=out64)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(k64):
-            plan64.zeldovich(seed=1 + i, out=out64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / k64
-        v64 = cells / (ms64 * 1e-3)
-        line["fp64"] = {"value": v64, "unit": "cells/s", "ms_per_step": ms64, "steps": k64,
-                        "fp32_speedup": (value / world) / v64}
         line["err_vs_fp64"] = {"psi_rel_l2": errs, "reference": "GPU FP64 path (within 1e-12 "
                                "of the FP64 oracle in tests/test_gpu_fullsize.py)"}
-        del out64, plan64
+        # the FP32 plan's workspaces make room for the FP64 pos + vel grids
+        # (174 GB at 1536^3); it is re-made for the end-to-end leg
+        plan.close()
+        plan = None
+        torch.cuda.empty_cache()
+        need = 6 * cells * 8 + (1 << 30)
+        out64, why = None, None
+        if torch.cuda.mem_get_info()[0] >= need:
+            out64 = {"psi": [None] * 3,
+                     "pos": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)],
+                     "vel": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)]}
+            try:  # the plan's own workspaces may still not fit: GG_ENOMEM, nothing launched
+                plan64.zeldovich(seed=1, out=out64)
+                torch.cuda.synchronize()
+            except gg.GGError as ex:
+                out64, why = None, str(ex)
+        else:
+            why = "FP64 pos + vel grids (%.0f GB) do not fit in device memory" % (need / 1e9)
+        if out64 is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(k64):
+                plan64.zeldovich(seed=1 + i, out=out64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1) / k64
+            v64 = cells / (ms64 * 1e-3)
+            line["fp64"] = {"value": v64, "unit": "cells/s", "ms_per_step": ms64, "steps": k64,
+                            "fp32_speedup": (value / world) / v64}
+            del out64
+        else:
+            line["fp64"] = {"skipped": why}
+        plan64.close()
+        del plan64
         torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: caller white noise
     # (the paper's "WN from file" input) up, positions and velocities down
     if not args.no_e2e:
+        if plan is None:
+            plan = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], w["prec"])
+            plan.set_variants(variants)
         hn = torch.randn(shape, dtype=dt).pin_memory()
         hout = {"psi": [None] * 3,
                 "pos": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)],
                 "vel": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)]}
-        del out
-        torch.cuda.empty_cache()
         ke = max(2, min(8, args.steps // 10))
         plan.zeldovich_host(noise=hn, out=hout)
         barrier()
@@ -624,7 +645,8 @@ def main():
 
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
-    plan.close()
+    if plan is not None:
+        plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -419,27 +419,12 @@ gg::AxisArgs axis_args(gg_plan_t *plan, int axis, const void *src) {
   return c;
 }
 
-// One strided pass; the size-specialised kernel where N has one. When that
-// kernel keeps one output per launch, a two-output pass becomes two launches
-// reading the same input, the in-place output (dst == src) last.
+// One strided pass; the size-specialised kernel where N has one. Every
+// output of a two-output pass comes from the one launch.
 template <typename R>
 gg_status launch_axis_timed(gg_plan_t *plan, const gg::AxisArgs &c, int kind, const char *what) {
   const double cb = (double)plan->cells * sizeof(R);
   const bool spec = gg::spec_has<R>(c.n);
-  const int max_out = spec ? gg::spec_axis_max_out<R>(c.n, c.variant) : 3;
-  if (c.inv && c.nout > max_out) {
-    int order[3] = {0, 1, 2};
-    if (c.nout == 2 && c.dst[0] == c.src) std::swap(order[0], order[1]);
-    for (int i = 0; i < c.nout; ++i) {
-      gg::AxisArgs one = c;
-      one.nout = 1;
-      one.dst[0] = c.dst[order[i]];
-      one.mul[0] = c.mul[order[i]];
-      gg_status st = launch_axis_timed<R>(plan, one, kind, what);
-      if (st != GG_OK) return st;
-    }
-    return GG_OK;
-  }
   const double bytes = (c.fwd && !c.inv ? 2 : 1 + c.nout) * cb;
   cudaError_t e;
   {

@@ -188,8 +188,9 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
 //   1: E doubled (two butterflies per thread and stage), rows of up to 128 bytes
 //   2: E doubled where it fits, rows halved (a smaller CTA: several share an
 //      SM, or two outputs fit the register budget)
-// Whether the handed-off spectrum of two outputs may stay in registers is
-// estimated from the register budget; otherwise one output per launch.
+// Whether the handed-off spectrum may stay in registers while an inverse
+// runs is estimated from the register budget; otherwise (SPILL) it is parked
+// in shared memory and every output reads it from there.
 template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int CB = 2 * (int)sizeof(R);
   static constexpr int E0 = elems(N);
@@ -212,7 +213,7 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int REG_BUDGET =
       65536 / (THREADS * MINB) < 255 ? 65536 / (THREADS * MINB) : 255;
   static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
-  static constexpr int MAX_OUT = REG_NEED <= REG_BUDGET ? 2 : 1;
+  static constexpr bool SPILL = REG_NEED > REG_BUDGET;
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
 };
 

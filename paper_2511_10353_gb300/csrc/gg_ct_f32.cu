@@ -5,7 +5,6 @@ namespace gg {
 
 using TableF32 = CtTable<float, 64, 128, 192, 256, 384, 512, 1536>;
 template <> bool spec_has<float>(int n) { return TableF32::has(n); }
-template <> int spec_axis_max_out<float>(int n, int v) { return TableF32::axis_max_out(n, v); }
 template <> cudaError_t spec_axis<float>(const AxisArgs &a, cudaStream_t s) { return TableF32::axis(a, s); }
 template <> cudaError_t spec_zinv<float>(const ZInvArgs &a, cudaStream_t s) { return TableF32::zinv(a, s); }
 template <> cudaError_t spec_zfwd<float>(const ZFwdArgs &a, cudaStream_t s) { return TableF32::zfwd(a, s); }

@@ -5,7 +5,6 @@ namespace gg {
 
 using TableF64 = CtTable<double, 64, 512, 1536>;
 template <> bool spec_has<double>(int n) { return TableF64::has(n); }
-template <> int spec_axis_max_out<double>(int n, int v) { return TableF64::axis_max_out(n, v); }
 template <> cudaError_t spec_axis<double>(const AxisArgs &a, cudaStream_t s) { return TableF64::axis(a, s); }
 template <> cudaError_t spec_zinv<double>(const ZInvArgs &a, cudaStream_t s) { return TableF64::zinv(a, s); }
 template <> cudaError_t spec_zfwd<double>(const ZFwdArgs &a, cudaStream_t s) { return TableF64::zfwd(a, s); }

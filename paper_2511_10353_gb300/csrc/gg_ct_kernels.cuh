@@ -16,6 +16,13 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // persistent CTAs, TMA double buffering, forward stages in place in shared
 // memory, the spectrum handed to the inverse stages in registers, each
 // inverse's last stage storing straight to HBM.
+// Where the handed-off spectrum and an inverse do not both fit the register
+// budget (Pol::SPILL), the spectrum is parked in the tile buffer at its
+// natural positions (each thread reads back only what it wrote) and every
+// output reads it from there. With several outputs the second buffer is then
+// the inverse work buffer, and the next tile's copy is issued into the first
+// once the last output has read the spectrum, overlapping that output's
+// inverse stages: all outputs come from one launch.
 template <typename R, int N, int V, bool CUT = false>
 __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
     k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
@@ -28,6 +35,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
   constexpr int RH = ct::radix_of(N, 0, true);  // radix at the register hand-off
   static_assert(RH == ct::radix_of(N, S - 1, false), "hand-off radix");
   constexpr int SPAN = N / RH, NB = E / RH;
+  constexpr bool SPILL = Pol::SPILL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
@@ -65,12 +73,16 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
       else tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, (int)outer, i, rr);
     }
   };
+  // late: one input buffer (0) and one work buffer (1); the copy of the next
+  // tile is issued during the last output
+  const bool late = SPILL && a.inv && a.nout > 1;
   int64_t t = blockIdx.x;
   if (tid == 0 && t < ntiles) issue(t, 0);
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-    const int sb = it & 1;
+    const int sb = late ? 0 : it & 1;
+    const uint32_t phase = late ? (uint32_t)(it & 1) : (uint32_t)((it >> 1) & 1);
     const int64_t tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) {
+    if (tid == 0 && tn < ntiles && !late) {
       fence_proxy_async_smem();
       issue(tn, sb ^ 1);
     }
@@ -82,6 +94,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     const int chunk = (int)(tt - outer * INNER);
     const int kz = chunk * B + c;
     C *buf = bufs + sb * TILE_STRIDE;
+    C *wb = late ? bufs + TILE_STRIDE : buf;  // the inverse work buffer
     const int64_t gbase = rr * a.batch_stride + outer * a.outer_stride + kz;
     const int m_outer = a.axis == 0 ? ct_freq((int)outer, N) : 0;
     const bool nyq_outer = a.axis == 0 && (int)outer == HALF;
@@ -98,18 +111,23 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
           if (q >= 0) prefetch_l1(table + q);
         }
     }
-    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err));
-    if (!ok) {
-      if (tid == 0 && tn < ntiles) mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], phase, a.err));
+    if (!ok) {  // late: no other copy is in flight
+      if (tid == 0 && tn < ntiles && !late)
+        mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
       return;
     }
     auto ld_smem = [&](int n) { return buf[n * B + c]; };
     auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
+    auto ld_work = [&](int n) { return wb[n * B + c]; };
+    auto st_work = [&](int n, C v) { wb[n * B + c] = v; };
+    // SPILL, inverse only, no filter: the spectrum is already parked
+    const bool x_regs = !SPILL || a.fwd || a.pre || !a.inv;
     C X[E];
     if (a.fwd) {
       ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
       ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, X);
-    } else {
+    } else if (x_regs) {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -153,7 +171,17 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
       __syncthreads();
       continue;
     }
-    __syncthreads();  // the tile is in registers: buf becomes the inverse work buffer
+    if constexpr (SPILL) {
+      if (a.fwd) __syncthreads();  // the forward's last stage has read the tile
+      if (x_regs) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) buf[(p + P * b + r * SPAN) * B + c] = X[b * RH + r];
+      }
+    } else {
+      __syncthreads();  // the tile is in registers: buf becomes the inverse work buffer
+    }
     for (int o = 0; o < a.nout; ++o) {
       asm volatile("" : "+r"(c), "+r"(p));
       C *d = reinterpret_cast<C *>(a.dst[o]) + gbase;
@@ -165,13 +193,19 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
           const int n = p + P * b + r * SPAN;
-          const C v = X[b * RH + r];
+          const C v = SPILL ? buf[n * B + c] : X[b * RH + r];
           const R f = n == HALF ? (R)0 : (R)ct_freq(n, N);
           W[b * RH + r] = im ? C{-f * v.y, f * v.x} : v;
         }
 #pragma unroll
       for (int b = 0; b < NB; ++b) Butterfly<RH, true, C>::run(&W[b * RH]);  // inverse stage 0
-      if (o > 0) __syncthreads();  // the previous output's last stage has read buf
+      // the previous output's last stage has read the work buffer; SPILL with
+      // one buffer: every thread has read its parked spectrum
+      if (o > 0 || (SPILL && !late)) __syncthreads();
+      if (late && o == a.nout - 1 && tid == 0 && tn < ntiles) {  // the input buffer is free
+        fence_proxy_async_smem();
+        issue(tn, 0);
+      }
       if constexpr (S == 1) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -181,10 +215,10 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-          for (int r = 0; r < RH; ++r) buf[((p + P * b) * RH + r) * B + c] = W[b * RH + r];
+          for (int r = 0; r < RH; ++r) wb[((p + P * b) * RH + r) * B + c] = W[b * RH + r];
         __syncthreads();
-        ct::stages<R, N, E, true, 1, S - 1>(p, tw, ld_smem, st_smem);
-        ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_smem, st_glob);
+        ct::stages<R, N, E, true, 1, S - 1>(p, tw, ld_work, st_work);
+        ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
       }
     }
     __syncthreads();
@@ -444,15 +478,6 @@ constexpr int kZVariants = 4;
 // Run-time dispatch over the specialised sizes and their tile variants.
 template <typename R, int... NS> struct CtTable {
   static bool has(int n) { return ((n == NS) || ...); }
-  template <int N> static int max_out_n(int v) {
-    return v == 0 ? ct::AxisPolicy<R, N, 0>::MAX_OUT
-                  : (v == 1 ? ct::AxisPolicy<R, N, 1>::MAX_OUT : ct::AxisPolicy<R, N, 2>::MAX_OUT);
-  }
-  static int axis_max_out(int n, int v) {
-    int m = 0;
-    ((m = (n == NS) ? max_out_n<NS>(v) : m), ...);
-    return m;
-  }
   template <int N> static cudaError_t axis_n(const AxisArgs &a, cudaStream_t s) {
     if (a.pre && a.qmin > 0) return ct_launch_axis<R, N, 0, true>(a, s);  // the Sec. 2.4 cut: variant 0
     return a.variant == 1 ? ct_launch_axis<R, N, 1>(a, s)

@@ -212,7 +212,6 @@ template <typename R> int max_block_threads_axis(int e);
 // Size-specialised kernels (gg_ct_f32.cu / gg_ct_f64.cu) for the grid sizes of
 // the named workloads; spec_has tells whether N has them.
 template <typename R> bool spec_has(int n);
-template <typename R> int spec_axis_max_out(int n, int variant);
 constexpr int kSpecAxisVariants = 3;  // tile variants the autotuner times per strided pass
 constexpr int kSpecZVariants = 4;     // ... per z pass
 template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
