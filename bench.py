@@ -558,7 +558,7 @@ def main():
             torch.cuda.synchronize()
             errs.append(float(torch.linalg.vector_norm(psi32.double() - psi64)
                               / torch.linalg.vector_norm(psi64)))
-        del psi64, psi32
+        del psi64, psi32, o64, o32
         line["err_vs_fp64"] = {"psi_rel_l2": errs, "reference": "GPU FP64 path (within 1e-12 "
                                "of the FP64 oracle in tests/test_gpu_fullsize.py)"}
         # the FP32 plan's workspaces make room for the FP64 pos + vel grids
@@ -620,8 +620,9 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             el = float(tt.item())
         esz = torch.finfo(dt).bits // 8
-        # the host link's own copy rates on the same pinned buffers: the step
-        # cannot beat h2d / rate_up + d2h / rate_down
+        # the copy engines' rates on the same pinned buffers, for scale: the
+        # step's outputs are written by the kernels themselves over the host
+        # link (mapped memory), which can beat the copies of a large buffer
         dev = torch.empty(shape, dtype=dt, device="cuda")
         rates = {}
         for name, fn in (("d2h", lambda: hout["pos"][0].copy_(dev, non_blocking=True)),
@@ -641,7 +642,7 @@ def main():
         line["e2e"] = {"value": world * cells * ke / el, "unit": "cells/s", "steps": ke,
                        "h2d_bytes_per_step": cells * esz, "d2h_bytes_per_step": 6 * cells * esz,
                        "api": "gg_zeldovich_host (pinned host noise in, pos/vel out)",
-                       "link_GB_s": rates, "frac_of_link_bound": bound_s / (el / ke)}
+                       "copy_GB_s": rates, "copy_time_over_step_time": bound_s / (el / ke)}
 
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)

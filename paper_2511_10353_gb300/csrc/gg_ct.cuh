@@ -178,6 +178,122 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
   }
 }
 
+// ------------------------------------------------------------ register pairs
+// A thread holds E elements: p + P*b + r*SPAN. Where E is a multiple of
+// RA*RB for the last two radices of the forward schedule (the first two of
+// the inverse), the thread's elements hold whole butterflies of both stages,
+// so the pair runs in registers without a shared-memory round trip between
+// them. Same twiddles, butterflies and order of operations as the two
+// separate stages.
+template <int N, int E> __host__ __device__ constexpr bool fuse_pair() {
+  return nstages(N) >= 3 && E % (radix_fwd(N, nstages(N) - 2) * radix_fwd(N, nstages(N) - 1)) == 0;
+}
+
+// Twiddles w^(k r), r = 1 .. RAD-1, on one butterfly's inputs; kt = k*TSTEP.
+template <typename R, int RAD, bool INV>
+__device__ __forceinline__ void stage_twiddle(Cx<R> *v, const Cx<R> *__restrict__ tw, int kt) {
+  if constexpr (sizeof(R) == 4) {
+    twiddle_powers<RAD, INV>(v, ldg_c(tw + kt));
+  } else {
+#pragma unroll
+    for (int r = 1; r < RAD; ++r) {
+      const Cx<R> w = ldg_c(tw + kt * r);
+      v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+  }
+}
+
+// The forward schedule's last two stages (A, B), outputs in registers with
+// the contract of last_stage_regs. Stage A's butterflies of this thread are
+// j = p + P*b, b = g + G*q (k = p + P*g, q < RB); their outputs are the inputs
+// of stage B's butterflies j' = p + P*(g + G*r), input q.
+template <typename R, int N, int E, class Ld>
+__device__ __forceinline__ void last_two_stages_regs(int p, const Cx<R> *__restrict__ tw,
+                                                     const Ld &ld, Cx<R> *v) {
+  constexpr int S = nstages(N);
+  constexpr int RA = radix_of(N, S - 2, false), RB = radix_of(N, S - 1, false);
+  constexpr int NSA = ns_of(N, S - 2, false);
+  constexpr int P = N / E, G = E / (RA * RB), NBA = E / RA, NBB = E / RB;
+  constexpr int SPANA = N / RA, TSA = N / (NSA * RA);
+  static_assert(NSA == P * G && NSA * RA * RB == N, "register pair");
+  asm volatile("" : "+r"(p));
+  Cx<R> w1[NBA];
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int b = 0; b < NBA; ++b) w1[b] = ldg_c(tw + k_of<NSA, P, NBA>(p, b) * TSA);
+  }
+  Cx<R> a[E];
+#pragma unroll
+  for (int b = 0; b < NBA; ++b)
+#pragma unroll
+    for (int r = 0; r < RA; ++r) a[b * RA + r] = ld(p + P * b + r * SPANA);
+#pragma unroll
+  for (int b = 0; b < NBA; ++b) {
+    if constexpr (NSA > 1) {
+      if constexpr (sizeof(R) == 4) twiddle_powers<RA, false>(&a[b * RA], w1[b]);
+      else stage_twiddle<R, RA, false>(&a[b * RA], tw, k_of<NSA, P, NBA>(p, b) * TSA);
+    }
+    Butterfly<RA, false, Cx<R>>::run(&a[b * RA]);
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+#pragma unroll
+      for (int r = 0; r < RA; ++r) v[(g + G * r) * RB + q] = a[(g + G * q) * RA + r];
+  // stage B: NS = N / RB, every j' < NS, so k = j' and TSTEP = 1
+#pragma unroll
+  for (int b = 0; b < NBB; ++b) {
+    stage_twiddle<R, RB, false>(&v[b * RB], tw, p + P * b);
+    Butterfly<RB, false, Cx<R>>::run(&v[b * RB]);
+  }
+}
+
+// The inverse schedule's first two stages (A: NS = 1, B: NS = RA) on
+// registers holding the hand-off layout (element p + P*b + r*N/RA at
+// v[b*RA + r]). Stage A's butterfly b = g + G*q feeds input q of stage B's
+// butterfly (g, r) = j' = p*RA + P*RA*g + r, whose k = r is known at compile
+// time. On return v[(g*RA + r)*RB + s] holds stage B's output s of butterfly
+// (g, r); inverse_head_store writes them.
+template <typename R, int N, int E>
+__device__ __forceinline__ void inverse_head_regs(const Cx<R> *__restrict__ tw, Cx<R> *v) {
+  constexpr int RA = radix_of(N, 0, true), RB = radix_of(N, 1, true);
+  constexpr int P = N / E, G = E / (RA * RB), NBA = E / RA;
+  constexpr int TSB = N / (RA * RB);
+#pragma unroll
+  for (int b = 0; b < NBA; ++b) Butterfly<RA, true, Cx<R>>::run(&v[b * RA]);
+  Cx<R> u[E];
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+#pragma unroll
+      for (int q = 0; q < RB; ++q) u[(g * RA + r) * RB + q] = v[(g + G * q) * RA + r];
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+      if (r > 0) stage_twiddle<R, RB, true>(&u[(g * RA + r) * RB], tw, r * TSB);
+      Butterfly<RB, true, Cx<R>>::run(&u[(g * RA + r) * RB]);
+    }
+#pragma unroll
+  for (int i = 0; i < E; ++i) v[i] = u[i];
+  (void)P;
+}
+// Stage B's outputs: element s of butterfly j' goes to (j' - k)*RB + k + s*RA.
+template <typename R, int N, int E, class St>
+__device__ __forceinline__ void inverse_head_store(int p, const Cx<R> *v, const St &st) {
+  constexpr int RA = radix_of(N, 0, true), RB = radix_of(N, 1, true);
+  constexpr int P = N / E, G = E / (RA * RB);
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+#pragma unroll
+      for (int s = 0; s < RB; ++s)
+        st(p * RA * RB + P * RA * RB * g + r + s * RA, v[(g * RA + r) * RB + s]);
+}
+
 // ------------------------------------------------------------ tile policy
 // Tile variants the autotuner chooses between (V = 0, 1, 2 for the strided
 // pass; V = 0, 1 for the z passes). An invalid variant for a size falls back

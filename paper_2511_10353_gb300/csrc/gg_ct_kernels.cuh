@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
   static_assert(RH == ct::radix_of(N, S - 1, false), "hand-off radix");
   constexpr int SPAN = N / RH, NB = E / RH;
   constexpr bool SPILL = Pol::SPILL;
+  constexpr bool FUSE = ct::fuse_pair<N, E>();  // stage pairs around the hand-off in registers
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
@@ -125,8 +126,13 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     const bool x_regs = !SPILL || a.fwd || a.pre || !a.inv;
     C X[E];
     if (a.fwd) {
-      ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
-      ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, X);
+      if constexpr (FUSE) {
+        ct::stages<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem);
+        ct::last_two_stages_regs<R, N, E>(p, tw, ld_smem, X);
+      } else {
+        ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
+        ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, X);
+      }
     } else if (x_regs) {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
@@ -197,8 +203,12 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
           const R f = n == HALF ? (R)0 : (R)ct_freq(n, N);
           W[b * RH + r] = im ? C{-f * v.y, f * v.x} : v;
         }
+      if constexpr (FUSE) {
+        ct::inverse_head_regs<R, N, E>(tw, W);  // inverse stages 0 and 1
+      } else {
 #pragma unroll
-      for (int b = 0; b < NB; ++b) Butterfly<RH, true, C>::run(&W[b * RH]);  // inverse stage 0
+        for (int b = 0; b < NB; ++b) Butterfly<RH, true, C>::run(&W[b * RH]);  // inverse stage 0
+      }
       // the previous output's last stage has read the work buffer; SPILL with
       // one buffer: every thread has read its parked spectrum
       if (o > 0 || (SPILL && !late)) __syncthreads();
@@ -211,6 +221,11 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
         for (int b = 0; b < NB; ++b)
 #pragma unroll
           for (int r = 0; r < RH; ++r) st_glob((p + P * b) * RH + r, W[b * RH + r]);
+      } else if constexpr (FUSE) {
+        ct::inverse_head_store<R, N, E>(p, W, st_work);
+        __syncthreads();
+        ct::stages<R, N, E, true, 2, S - 1>(p, tw, ld_work, st_work);
+        ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
       } else {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
