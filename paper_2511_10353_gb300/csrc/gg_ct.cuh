@@ -344,11 +344,17 @@ template <typename R, int N, int V> struct ZPolicy {
   static constexpr int P = M / E;
   static constexpr int CB = 2 * (int)sizeof(R);
   static constexpr int LD = M + (M >> 4) + 1;  // tile sizing (the widest padding)
+  // the forward's last two and the inverse's first two stages in registers
+  static constexpr bool FUSE = fuse_pair<M, E>();
   // Padding of the work tile, per direction: one empty slot every PAD values
   // (0: none). Chosen by counting the shared-memory wavefronts of every
   // stage's stores and loads for each size; FP32 (FP64 keeps 1 in 16).
   static constexpr int pad_of(bool inv) {
     if (sizeof(R) != 4) return 16;
+    if (inv && FUSE) {             // register pair first: its stores are 12-24 apart
+      if (M == 768) return 32;         // 248 wavefronts a line instead of 360 unpadded
+      if (M == 192 || M == 96) return 64;
+    }
     if (M == 96) return 32;           // N = 192: 1.2x / 1.5x the minimum instead of 2x
     if (inv && M == 768) return 0;    // N = 1536 inverse: 1.25x instead of 1.48x
     return 16;

@@ -295,6 +295,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     if (!ok) return;  // nothing else in flight: the next copy is issued after this wait
     const C *dl = dense + l * M;
     const R pf = (R)p;  // (R)(p + c) == pf + (R)c exactly: small integers
+    auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
+    auto st_w = [&](int n, C v) { work[zpad<LD, PAD>(l, n)] = v; };
+    C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k = p + P * i;
@@ -307,17 +310,24 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       }
       const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
       const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
-      work[zpad<LD, PAD>(l, k)] = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
+      const C z = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
+      if constexpr (Pol::FUSE) {  // k = p + P*(b + (E/RA)*r): the first stage's layout
+        constexpr int RA = ct::radix_of(M, 0, true), NBA = E / RA;
+        v[(i % NBA) * RA + i / NBA] = z;
+      } else {
+        st_w(k, z);
+      }
+    }
+    if constexpr (Pol::FUSE) {  // the inverse's first two stages in registers
+      ct::inverse_head_regs<R, M, E>(tw_half, v);
+      ct::inverse_head_store<R, M, E>(p, v, st_w);
     }
     __syncthreads();
     if (tid == 0 && tn < ntiles) {  // the dense buffer has been read: fetch the next block
       fence_proxy_async_smem();
       issue(tn);
     }
-    auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
-    auto st_w = [&](int n, C v) { work[zpad<LD, PAD>(l, n)] = v; };
-    ct::stages<R, M, E, true, 0, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
-    C v[E];
+    ct::stages<R, M, E, true, Pol::FUSE ? 2 : 0, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
     ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
     // line -> (realization, x, y): line counts stay below 2^32 (N <= 4096, the
     // host bounds the batch), so 32-bit divisions suffice
@@ -426,7 +436,20 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     ct::stage_barrier<Pol::SY>();
     auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
     auto st_w = [&](int n, C v) { work[zpad<LD, PAD>(l, n)] = v; };
-    ct::stages<R, M, E, false, 0, S, Pol::SY>(p, tw_half, ld_w, st_w);
+    if constexpr (Pol::FUSE) {  // the last two stages in registers, stored in natural order
+      ct::stages<R, M, E, false, 0, S - 2, Pol::SY>(p, tw_half, ld_w, st_w);
+      constexpr int RB = ct::radix_of(M, S - 1, false), NBB = E / RB, SPANB = M / RB;
+      C v[E];
+      ct::last_two_stages_regs<R, M, E>(p, tw_half, ld_w, v);
+      ct::stage_barrier<Pol::SY>();
+#pragma unroll
+      for (int b = 0; b < NBB; ++b)
+#pragma unroll
+        for (int r = 0; r < RB; ++r) st_w(p + P * b + r * SPANB, v[b * RB + r]);
+      ct::stage_barrier<Pol::SY>();
+    } else {
+      ct::stages<R, M, E, false, 0, S, Pol::SY>(p, tw_half, ld_w, st_w);
+    }
     C *dst = reinterpret_cast<C *>(a.out) + line * M;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
