@@ -322,9 +322,9 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int B = pick();
   static constexpr int THREADS = P * B;
   // variant 2 (small CTAs): register bound for two CTAs per SM where the
-  // shared memory (two tiles, FP32 filter table) lets two fit
-  static constexpr int SMEM_EST = 128 + 2 * N * B * CB +
-                                  (sizeof(R) == 4 ? 4096 + 16 * (N + N / 2 + 8) : 0);
+  // shared memory of two tiles lets two fit (the FP32 filter table of the x
+  // pass may still keep that pass at one)
+  static constexpr int SMEM_EST = 128 + 2 * N * B * CB;
   static constexpr int MINB = (V == 2 && THREADS <= 256 && 2 * SMEM_EST <= 227 * 1024) ? 2 : 1;
   static constexpr int REG_BUDGET =
       65536 / (THREADS * MINB) < 255 ? 65536 / (THREADS * MINB) : 255;
