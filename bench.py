@@ -40,6 +40,9 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_TRAFFIC = {
     # profiles/z_inverse_512_fp32_ncu.md: 536,954,368 B read + 1,017,026,304 B written
     ("z_inverse_epilogue", "zeldovich_512_fp32"): (1553980672.0, "4002694f49da3de5"),
+    # profiles/counters_zeldovich_1536_fp32.md (one-pass metrics at full size):
+    # 14,496,350,976 B read + 28,931,635,200 B written, first of the three launches
+    ("z_inverse_epilogue", "zeldovich_1536_fp32"): (43427986176.0, "4002694f49da3de5"),
 }
 
 
