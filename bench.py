@@ -39,18 +39,23 @@ FALLBACK_HBM_GBS = 6800.0
 # was taken on; reported as null when the sources have changed since.
 NCU_TRAFFIC = {
     # profiles/z_inverse_512_fp32_ncu.md: 536,954,368 B read + 1,017,026,304 B written
-    ("z_inverse_epilogue", "zeldovich_512_fp32"): (1553980672.0, "4002694f49da3de5"),
+    ("z_inverse_epilogue", "zeldovich_512_fp32"): (1553980672.0, "f4c95b4e3f04949c"),
     # profiles/counters_zeldovich_1536_fp32.md (one-pass metrics at full size):
     # 14,496,350,976 B read + 28,931,635,200 B written, first of the three launches
-    ("z_inverse_epilogue", "zeldovich_1536_fp32"): (43427986176.0, "4002694f49da3de5"),
+    ("z_inverse_epilogue", "zeldovich_1536_fp32"): (43427986176.0, "f4c95b4e3f04949c"),
 }
 
 
 def kernel_source_hash():
+    """Hash of the kernel headers' code (// comments and blank lines left out,
+    so that a comment edit keeps the recorded ncu traffic valid)."""
     h = hashlib.sha256()
     for f in ("gg_device.cuh", "gg_kernels.cuh", "gg_ct.cuh", "gg_ct_kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_2511_10353_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2511_10353_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -251,10 +251,12 @@ template <int LD, int PAD> __device__ __forceinline__ int zpad(int l, int n) {
 
 // Inverse z pass (c2r) + Eq. 3 epilogue, persistent: one thread bulk-copies
 // a block of L contiguous half-spectrum lines into a dense shared buffer. The
-// c2r pre-processing moves it into the padded work tile, after which the
-// buffer is free and the copy of the CTA's next block starts; it lands while
-// the transform and the epilogue of the current block run. The last stage's
-// outputs (natural order) feed the epilogue from registers.
+// c2r pre-processing moves it into the padded work tile (where the first two
+// inverse stages pair up, through them in registers: the pre-processing
+// yields exactly the first stage's inputs), after which the buffer is free
+// and the copy of the CTA's next block starts; it lands while the transform
+// and the epilogue of the current block run. The last stage's outputs
+// (natural order) feed the epilogue from registers.
 // EXT: the Sec. 2.4 merge (large) and the Sec. 2.2 particle options (shift,
 // pos2), compiled only into the extended instantiation.
 template <typename R, int N, int V, bool EXT = false>
