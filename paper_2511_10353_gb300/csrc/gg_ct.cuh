@@ -140,6 +140,20 @@ __device__ __forceinline__ void stages(int p, const Cx<R> *__restrict__ tw, cons
   }
 }
 
+// Stages FIRST .. LAST-1 alternating between two shared buffers (FIRST reads
+// A and writes B, the next reads B and writes A, ...): one CTA barrier per
+// stage instead of two. The caller leaves B free; an even count ends in A.
+template <typename R, int N, int E, bool INV, int FIRST, int LAST, class LdA, class StA, class LdB,
+          class StB>
+__device__ __forceinline__ void stages_pingpong(int p, const Cx<R> *__restrict__ tw, const LdA &lda,
+                                                const StA &sta, const LdB &ldb, const StB &stb) {
+  if constexpr (FIRST < LAST) {
+    stage<R, N, E, FIRST, INV, kSyncNone>(p, tw, lda, stb);
+    __syncthreads();
+    stages_pingpong<R, N, E, INV, FIRST + 1, LAST>(p, tw, ldb, stb, lda, sta);
+  }
+}
+
 // The last stage of a schedule, outputs kept in registers: on return v holds
 // element j + r*N/RAD at v[b*RAD + r] (j = p + P*b).
 template <typename R, int N, int E, bool INV, class Ld>

@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     C X[E];
     if (a.fwd) {
       if constexpr (FUSE) {
-        ct::stages<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem);
+        if ((S - 2) % 2 == 0 && late)  // the work buffer is free: ping-pong, ending in buf
+          ct::stages_pingpong<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem, ld_work, st_work);
+        else
+          ct::stages<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem);
         ct::last_two_stages_regs<R, N, E>(p, tw, ld_smem, X);
       } else {
         ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
