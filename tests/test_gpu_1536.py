@@ -9,7 +9,9 @@ this size, so:
   with s from the oracle's P(k0) and growth, checked on sampled cells;
 * each displacement component of the FP32 path is within 1e-5 relative L2
   of the GPU FP64 path (which the other tests pin to the oracle at <= 1e-12);
-* the strided passes' tile variants agree bit for bit.
+* the strided passes' tile variants agree bit for bit;
+* Eq. 4's top hat at this size: the planted mode comes out unchanged above
+  the cut and vanishes below it.
 """
 import math
 
@@ -134,5 +136,42 @@ def test_strided_variants_bit_identical(gg):
                 assert torch.equal(cur[j], ref[j]), (a, j)
     assert float(ref[0].abs().max()) > 0.0
     del ref, cur
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def test_merge_cut_planted_mode(gg):
+    """Eq. 4 on the full-size grid (the x pass's cut instantiation, with the
+    spectrum parked in shared memory and both outputs from one launch): with
+    no coarse grids to add, a planted mode with |k0| r_s >= 1 gives the plain
+    path's analytic displacement and one with |k0| r_s < 1 gives zero."""
+    from tests.oracle_cases import cosmology_from
+    c = cosmology_from(EH_NW)
+    m0 = (3, -7, 11)
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f32")
+    i = torch.arange(N, device="cuda", dtype=torch.float64)
+    ph = (2 * math.pi / N) * (m0[0] * i[:, None, None] + m0[1] * i[None, :, None])
+    noise = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    for ix in range(0, N, 64):
+        noise[ix:ix + 64] = torch.cos(ph[ix:ix + 64] + (2 * math.pi / N) * m0[2] * i[None, None, :]).float()
+    del ph
+    psi = [torch.empty((N, N, N), dtype=torch.float32, device="cuda") for _ in range(3)]
+    idx = _sample_idx(100000, 2)
+    ix, iy, iz = idx // (N * N), (idx // N) % N, idx % N
+    phase = 2 * math.pi * (m0[0] * ix + m0[1] * iy + m0[2] * iz) / N
+    k0 = 2 * math.pi / BOX * np.array(m0, dtype=float)
+    kk = math.sqrt((k0 ** 2).sum())
+    s = plan.info["growth"] * math.sqrt(c.power(kk) * N ** 3 / BOX ** 3)
+    it = torch.from_numpy(idx).cuda()
+    for r_s in (2.0 / kk, 0.5 / kk):  # kept, removed
+        plan.zeldovich_merge([None] * 3, r_s, noise=noise,
+                             out={"psi": psi, "pos": [None] * 3, "vel": [None] * 3})
+        plan.sync()
+        for j in range(3):
+            got = psi[j].reshape(-1)[it].cpu().numpy().astype(np.float64)
+            scale = s * abs(k0[j]) / kk ** 2
+            want = -s * k0[j] / kk ** 2 * np.sin(phase) if r_s * kk >= 1 else 0.0 * phase
+            assert np.abs(got - want).max() < 2e-5 * scale, (r_s, j)
+    del noise, psi
     plan.close()
     torch.cuda.empty_cache()
