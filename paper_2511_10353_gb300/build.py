@@ -23,7 +23,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = [
     "gg_ct_f32.cu",
+    "gg_ct_z_f32.cu",
     "gg_ct_f64.cu",
+    "gg_ct_z_f64.cu",
     "gg_axis_f32.cu",
     "gg_axis_f64.cu",
     "gg_kernels_f32.cu",

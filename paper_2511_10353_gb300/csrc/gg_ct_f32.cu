@@ -1,4 +1,6 @@
-// F32 size-specialised kernels for N = 64, 128, 192, 256, 384, 512, 1536.
+// F32 size-specialised strided-pass kernels for N = 64, 128, 192, 256, 384,
+// 512, 1536 (the z-pass kernels of the same sizes are in gg_ct_z_f32.cu: two
+// translation units that compile in parallel).
 #include "gg_ct_kernels.cuh"
 
 namespace gg {
@@ -6,7 +8,5 @@ namespace gg {
 using TableF32 = CtTable<float, 64, 128, 192, 256, 384, 512, 1536>;
 template <> bool spec_has<float>(int n) { return TableF32::has(n); }
 template <> cudaError_t spec_axis<float>(const AxisArgs &a, cudaStream_t s) { return TableF32::axis(a, s); }
-template <> cudaError_t spec_zinv<float>(const ZInvArgs &a, cudaStream_t s) { return TableF32::zinv(a, s); }
-template <> cudaError_t spec_zfwd<float>(const ZFwdArgs &a, cudaStream_t s) { return TableF32::zfwd(a, s); }
 
 }  // namespace gg

@@ -1,4 +1,6 @@
-// F64 size-specialised kernels for N = 64, 512, 1536.
+// F64 size-specialised strided-pass kernels for N = 64, 512, 1536 (the z-pass
+// kernels of the same sizes are in gg_ct_z_f64.cu: two translation units
+// that compile in parallel).
 #include "gg_ct_kernels.cuh"
 
 namespace gg {
@@ -6,7 +8,5 @@ namespace gg {
 using TableF64 = CtTable<double, 64, 512, 1536>;
 template <> bool spec_has<double>(int n) { return TableF64::has(n); }
 template <> cudaError_t spec_axis<double>(const AxisArgs &a, cudaStream_t s) { return TableF64::axis(a, s); }
-template <> cudaError_t spec_zinv<double>(const ZInvArgs &a, cudaStream_t s) { return TableF64::zinv(a, s); }
-template <> cudaError_t spec_zfwd<double>(const ZFwdArgs &a, cudaStream_t s) { return TableF64::zfwd(a, s); }
 
 }  // namespace gg

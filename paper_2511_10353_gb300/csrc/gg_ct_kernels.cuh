@@ -23,10 +23,14 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // the inverse work buffer, and the next tile's copy is issued into the first
 // once the last output has read the spectrum, overlapping that output's
 // inverse stages: all outputs come from one launch.
-template <typename R, int N, int V, bool CUT = false>
+// MODE (kAxisFwd, kAxisInv, kAxisFwdInv) fixes at compile time which halves
+// run (the flags a.fwd, a.inv are not read): each kernel holds only its path.
+constexpr int kAxisFwd = 1, kAxisInv = 2, kAxisFwdInv = 3;
+template <typename R, int N, int V, int MODE, bool CUT = false>
 __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
     k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
   using C = Cx<R>;
+  constexpr bool FWD = MODE != kAxisInv, INV = MODE != kAxisFwd;
   using Pol = ct::AxisPolicy<R, N, V>;
   constexpr int B = Pol::B, E = Pol::E, P = Pol::P, HALF = N / 2, S = ct::nstages(N);
   constexpr int TILE = N * B;
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
   };
   // late: one input buffer (0) and one work buffer (1); the copy of the next
   // tile is issued during the last output
-  const bool late = SPILL && a.inv && a.nout > 1;
+  const bool late = SPILL && INV && a.nout > 1;
   int64_t t = blockIdx.x;
   if (tid == 0 && t < ntiles) issue(t, 0);
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
@@ -123,9 +127,9 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     auto ld_work = [&](int n) { return wb[n * B + c]; };
     auto st_work = [&](int n, C v) { wb[n * B + c] = v; };
     // SPILL, inverse only, no filter: the spectrum is already parked
-    const bool x_regs = !SPILL || a.fwd || a.pre || !a.inv;
+    const bool x_regs = !SPILL || FWD || a.pre || !INV;
     C X[E];
-    if (a.fwd) {
+    if constexpr (FWD) {
       if constexpr (FUSE) {
         if ((S - 2) % 2 == 0 && late)  // the work buffer is free: ping-pong, ending in buf
           ct::stages_pingpong<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem, ld_work, st_work);
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
           X[b * RH + r] = C{f * X[b * RH + r].x, f * X[b * RH + r].y};
         }
     }
-    if (!a.inv) {  // forward only: the spectrum to dst[0]
+    if constexpr (!INV) {  // forward only: the spectrum to dst[0]
       C *d = reinterpret_cast<C *>(a.dst[0]) + gbase;
 #pragma unroll
       for (int b = 0; b < NB; ++b)
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
       continue;
     }
     if constexpr (SPILL) {
-      if (a.fwd) __syncthreads();  // the forward's last stage has read the tile
+      if constexpr (FWD) __syncthreads();  // the forward's last stage has read the tile
       if (x_regs) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
 }
 
 // ------------------------------------------------------------ launchers
-template <typename R, int N, int V, bool CUT = false>
+template <typename R, int N, int V, int MODE, bool CUT = false>
 cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   using Pol = ct::AxisPolicy<R, N, V>;
   AxisArgs a = in;
@@ -485,7 +489,7 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   const bool interp = sizeof(R) == 4 && a.pre && a.interp;
   const size_t smem = 128 + 2 * tile +
                       (interp ? kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16 : 0);
-  auto kern = k_axis_ct<R, N, V, CUT>;
+  auto kern = k_axis_ct<R, N, V, MODE, CUT>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, tiles), Pol::THREADS, smem, s>>>(map, a);
@@ -521,10 +525,17 @@ constexpr int kZVariants = 4;
 // Run-time dispatch over the specialised sizes and their tile variants.
 template <typename R, int... NS> struct CtTable {
   static bool has(int n) { return ((n == NS) || ...); }
+  template <int N, int V> static cudaError_t axis_v(const AxisArgs &a, cudaStream_t s) {
+    if (a.fwd && a.inv) return ct_launch_axis<R, N, V, kAxisFwdInv>(a, s);
+    return a.fwd ? ct_launch_axis<R, N, V, kAxisFwd>(a, s) : ct_launch_axis<R, N, V, kAxisInv>(a, s);
+  }
   template <int N> static cudaError_t axis_n(const AxisArgs &a, cudaStream_t s) {
-    if (a.pre && a.qmin > 0) return ct_launch_axis<R, N, 0, true>(a, s);  // the Sec. 2.4 cut: variant 0
-    return a.variant == 1 ? ct_launch_axis<R, N, 1>(a, s)
-                          : (a.variant == 2 ? ct_launch_axis<R, N, 2>(a, s) : ct_launch_axis<R, N, 0>(a, s));
+    if (!a.fwd && !a.inv) return cudaErrorInvalidValue;
+    if (a.pre && a.qmin > 0) {  // the Sec. 2.4 cut (the fused x pass only): variant 0
+      if (!(a.fwd && a.inv)) return cudaErrorInvalidValue;
+      return ct_launch_axis<R, N, 0, kAxisFwdInv, true>(a, s);
+    }
+    return a.variant == 1 ? axis_v<N, 1>(a, s) : (a.variant == 2 ? axis_v<N, 2>(a, s) : axis_v<N, 0>(a, s));
   }
   static cudaError_t axis(const AxisArgs &a, cudaStream_t s) {
     cudaError_t e = cudaErrorInvalidValue;
