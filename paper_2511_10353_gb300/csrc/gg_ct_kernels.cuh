@@ -425,14 +425,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     // line counts stay below 2^32 (N <= 4096, the host bounds the batch)
     const uint32_t lpr = (uint32_t)(a.lines_per_real > 0 ? a.lines_per_real : a.nlines);
     const uint32_t rr = (uint32_t)line / lpr, local = (uint32_t)line - rr * lpr;
-    const uint64_t seed = a.seeds ? a.seeds[rr] : a.seed;
-    if (a.noise) {
-      const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
-#pragma unroll
-      for (int i = 0; i < E; ++i) work[zpad<LD, PAD>(l, p + P * i)] = src[p + P * i];
-    } else {
-      static_assert(N % 4 == 0, "lines start on a Philox group");
-      const uint64_t g0 = (uint64_t)local * (uint64_t)(N / 4);
+    static_assert(N % 4 == 0, "lines start on a Philox group");
+    const uint64_t g0 = (uint64_t)local * (uint64_t)(N / 4);
+    auto gen = [&](uint64_t seed) {
 #pragma unroll
       for (int i = 0; i < E / 2; ++i) {
         const int q = p + P * i;
@@ -441,6 +436,15 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
         work[zpad<LD, PAD>(l, 2 * q)] = C{w[0], w[1]};
         work[zpad<LD, PAD>(l, 2 * q + 1)] = C{w[2], w[3]};
       }
+    };
+    if (a.noise) {
+      const C *src = reinterpret_cast<const C *>(a.noise) + line * M;
+#pragma unroll
+      for (int i = 0; i < E; ++i) work[zpad<LD, PAD>(l, p + P * i)] = src[p + P * i];
+    } else if (!a.seeds) {  // one seed for the launch: its key schedule is uniform
+      gen(a.seed);
+    } else {
+      gen(a.seeds[rr]);
     }
     ct::stage_barrier<Pol::SY>();
     auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
