@@ -266,7 +266,12 @@ template <int LD, int PAD> __device__ __forceinline__ int zpad(int l, int n) {
 // (natural order) feed the epilogue from registers.
 // EXT: the Sec. 2.4 merge (large) and the Sec. 2.2 particle options (shift,
 // pos2), compiled only into the extended instantiation.
-template <typename R, int N, int V, bool EXT = false>
+// OUT: 0 reads the outputs and the component from the arguments; kZPosVel
+// (x or y component) and kZPosVelZ (z component, i m_z) fix the plain
+// path's pos + vel outputs at compile time (no psi, no accumulation, no
+// per-realization pointer lists).
+constexpr int kZPosVel = 1, kZPosVelZ = 2;
+template <typename R, int N, int V, bool EXT = false, int OUT = 0>
 __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_INV)
     k_zinv_ct(const ZInvArgs a) {
   using C = Cx<R>;
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       const int k = p + P * i;
       C xk = dl[k];
       C xm = k ? dl[M - k] : C{(R)0, (R)0};
-      if (a.mul_kz) {  // i m_z on both members of the pair
+      if (OUT == 0 ? a.mul_kz != 0 : OUT == kZPosVelZ) {  // i m_z on both members of the pair
         const R kf = pf + (R)(P * i), mf = (R)M - kf;
         xk = C{-kf * xk.y, kf * xk.x};
         xm = C{-mf * xm.y, mf * xm.x};
@@ -344,12 +349,13 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     const uint32_t lpr = (uint32_t)(a.lines_per_real > 0 ? a.lines_per_real : a.nlines);
     const uint32_t rr = line / lpr, local = line - rr * lpr;
     const uint32_t ix = local / (uint32_t)a.n, iy = local - ix * (uint32_t)a.n;
-    const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
+    const int comp = OUT == 0 ? a.comp : (OUT == kZPosVelZ ? 2 : a.comp);
+    const R qline = comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
     const R q2p = (R)(2 * p);  // (R)(2n) == q2p + (R)(2n - 2p) exactly
-    void *psi_b = a.psi_list ? a.psi_list[rr] : a.psi;
-    void *pos_b = a.pos_list ? a.pos_list[rr] : a.pos;
-    void *vel_b = a.vel_list ? a.vel_list[rr] : a.vel;
-    const int64_t off = (int64_t)((a.psi_list || a.pos_list || a.vel_list) ? local : line) * M;
+    void *psi_b = OUT ? nullptr : (a.psi_list ? a.psi_list[rr] : a.psi);
+    void *pos_b = OUT ? a.pos : (a.pos_list ? a.pos_list[rr] : a.pos);
+    void *vel_b = OUT ? a.vel : (a.vel_list ? a.vel_list[rr] : a.vel);
+    const int64_t off = (int64_t)((!OUT && (a.psi_list || a.pos_list || a.vel_list)) ? local : line) * M;
     C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
     C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
     C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
             z.y += l1;
           }
         }
-        if (psi) {
+        if (!OUT && psi) {
           if (a.accumulate) {
             const C o = psi[n];
             psi[n] = C{o.x + (R)a.alpha * z.x, o.y + (R)a.alpha * z.y};
@@ -383,9 +389,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
             psi[n] = z;
           }
         }
-        if (pos) {
+        if (OUT || pos) {
           R q0 = qline, q1 = qline;
-          if (a.comp == 2) {
+          if (comp == 2) {
             q0 = (q2p + (R)(2 * (n - p)) + qo) * cell;
             q1 = (q2p + (R)(2 * (n - p) + 1) + qo) * cell;
           }
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
             pos[n] = C{wrap_box<R>(q0 + z.x, box), wrap_box<R>(q1 + z.y, box)};
           }
         }
-        if (vel) vel[n] = C{vfac * z.x, vfac * z.y};
+        if (OUT || vel) vel[n] = C{vfac * z.x, vfac * z.y};
       }
     ct::stage_barrier<Pol::SY>();  // the work tile's lines are rewritten next tile
   }
@@ -500,12 +506,12 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename R, int N, int V, bool EXT = false>
+template <typename R, int N, int V, bool EXT = false, int OUT = 0>
 cudaError_t ct_launch_zinv(const ZInvArgs &a, cudaStream_t s) {
   using Pol = ct::ZPolicy<R, N, V>;
   const size_t dense = (Pol::DENSE * 2 * sizeof(R) + 127) & ~(size_t)127;
   const size_t smem = 128 + dense + (size_t)Pol::WORK_INV * 2 * sizeof(R);
-  auto kern = k_zinv_ct<R, N, V, EXT>;
+  auto kern = k_zinv_ct<R, N, V, EXT, OUT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, a.nlines / Pol::L), Pol::THREADS, smem, s>>>(a);
@@ -546,14 +552,21 @@ template <typename R, int... NS> struct CtTable {
     ((a.n == NS ? (e = axis_n<NS>(a, s), 0) : 0), ...);
     return e;
   }
+  template <int N, int V> static cudaError_t zinv_v(const ZInvArgs &a, cudaStream_t s) {
+    const bool plain = !a.psi && a.pos && a.vel && !a.accumulate && !a.psi_list && !a.pos_list &&
+                       !a.vel_list && (a.mul_kz != 0) == (a.comp == 2);
+    if (!plain) return ct_launch_zinv<R, N, V>(a, s);
+    return a.comp == 2 ? ct_launch_zinv<R, N, V, false, kZPosVelZ>(a, s)
+                       : ct_launch_zinv<R, N, V, false, kZPosVel>(a, s);
+  }
   template <int N> static cudaError_t zinv_n(const ZInvArgs &a, cudaStream_t s) {
     if (a.large || a.pos2 || a.shift != 0.0 || a.shift2 != 0.0)  // Secs. 2.2, 2.4 options: variant 0
       return ct_launch_zinv<R, N, 0, true>(a, s);
     switch (a.variant) {
-      case 1: return ct_launch_zinv<R, N, 1>(a, s);
-      case 2: return ct_launch_zinv<R, N, 2>(a, s);
-      case 3: return ct_launch_zinv<R, N, 3>(a, s);
-      default: return ct_launch_zinv<R, N, 0>(a, s);
+      case 1: return zinv_v<N, 1>(a, s);
+      case 2: return zinv_v<N, 2>(a, s);
+      case 3: return zinv_v<N, 3>(a, s);
+      default: return zinv_v<N, 0>(a, s);
     }
   }
   template <int N> static cudaError_t zfwd_n(const ZFwdArgs &a, cudaStream_t s) {
