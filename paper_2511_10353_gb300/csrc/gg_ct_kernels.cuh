@@ -25,8 +25,11 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // inverse stages: all outputs come from one launch.
 // MODE (kAxisFwd, kAxisInv, kAxisFwdInv) fixes at compile time which halves
 // run (the flags a.fwd, a.inv are not read): each kernel holds only its path.
+// INTERP: the handed-off spectrum is always filtered by the interpolated
+// FP32 table in shared memory at a.interp (the fused x pass of the plain
+// path); a.pre is then not read.
 constexpr int kAxisFwd = 1, kAxisInv = 2, kAxisFwdInv = 3;
-template <typename R, int N, int V, int MODE, bool CUT = false>
+template <typename R, int N, int V, int MODE, bool CUT = false, bool INTERP = false>
 __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
     k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
   using C = Cx<R>;
@@ -52,7 +55,9 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
   const int64_t ntiles = per_real * (a.nbatch > 0 ? a.nbatch : 1);
   const C *tw = reinterpret_cast<const C *>(a.tw);
   const R *table = reinterpret_cast<const R *>(a.table);
-  const bool interp = sizeof(R) == 4 && a.pre && a.interp;
+  static_assert(!INTERP || sizeof(R) == 4, "interpolated filter: FP32");
+  const bool pre = INTERP || a.pre;
+  const bool interp = INTERP || (sizeof(R) == 4 && a.pre && a.interp);
   if (interp) {
     const float *src = reinterpret_cast<const float *>(a.interp);
     for (int i = tid; i < kInterpExact; i += blockDim.x) f_exact[i] = src[i];
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
       const int m = ct_freq(n, N);
       return (n == HALF || nyq_outer) ? -1 : m * m + m_outer * m_outer + kz * kz;
     };
-    if (a.pre && !interp) {
+    if (pre && !interp) {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     auto ld_work = [&](int n) { return wb[n * B + c]; };
     auto st_work = [&](int n, C v) { wb[n * B + c] = v; };
     // SPILL, inverse only, no filter: the spectrum is already parked
-    const bool x_regs = !SPILL || FWD || a.pre || !INV;
+    const bool x_regs = !SPILL || FWD || pre || !INV;
     C X[E];
     if constexpr (FWD) {
       if constexpr (FUSE) {
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
 #pragma unroll
         for (int r = 0; r < RH; ++r) X[b * RH + r] = buf[(p + P * b + r * SPAN) * B + c];
     }
-    if (a.pre) {
+    if (pre) {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
 }
 
 // ------------------------------------------------------------ launchers
-template <typename R, int N, int V, int MODE, bool CUT = false>
+template <typename R, int N, int V, int MODE, bool CUT = false, bool INTERP = false>
 cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   using Pol = ct::AxisPolicy<R, N, V>;
   AxisArgs a = in;
@@ -499,7 +504,7 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   const bool interp = sizeof(R) == 4 && a.pre && a.interp;
   const size_t smem = 128 + 2 * tile +
                       (interp ? kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16 : 0);
-  auto kern = k_axis_ct<R, N, V, MODE, CUT>;
+  auto kern = k_axis_ct<R, N, V, MODE, CUT, INTERP>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);
   kern<<<persistent_blocks(kern, Pol::THREADS, smem, tiles), Pol::THREADS, smem, s>>>(map, a);
@@ -536,7 +541,11 @@ constexpr int kZVariants = 4;
 template <typename R, int... NS> struct CtTable {
   static bool has(int n) { return ((n == NS) || ...); }
   template <int N, int V> static cudaError_t axis_v(const AxisArgs &a, cudaStream_t s) {
-    if (a.fwd && a.inv) return ct_launch_axis<R, N, V, kAxisFwdInv>(a, s);
+    if (a.fwd && a.inv) {
+      if constexpr (sizeof(R) == 4)
+        if (a.pre && a.interp) return ct_launch_axis<R, N, V, kAxisFwdInv, false, true>(a, s);
+      return ct_launch_axis<R, N, V, kAxisFwdInv>(a, s);
+    }
     return a.fwd ? ct_launch_axis<R, N, V, kAxisFwd>(a, s) : ct_launch_axis<R, N, V, kAxisInv>(a, s);
   }
   template <int N> static cudaError_t axis_n(const AxisArgs &a, cudaStream_t s) {
