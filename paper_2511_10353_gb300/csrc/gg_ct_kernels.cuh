@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       C xm = k ? dl[M - k] : C{(R)0, (R)0};
       if (OUT == 0 ? a.mul_kz != 0 : OUT == kZPosVelZ) {  // i m_z on both members of the pair
         const R kf = pf + (R)(P * i), mf = (R)M - kf;
-        xk = C{-kf * xk.y, kf * xk.x};
-        xm = C{-mf * xm.y, mf * xm.x};
+        xk = C{mul_rn(-kf, xk.y), mul_rn(kf, xk.x)};
+        xm = C{mul_rn(-mf, xm.y), mul_rn(mf, xm.x)};
       }
       const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
       const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     const uint32_t rr = line / lpr, local = line - rr * lpr;
     const uint32_t ix = local / (uint32_t)a.n, iy = local - ix * (uint32_t)a.n;
     const int comp = OUT == 0 ? a.comp : (OUT == kZPosVelZ ? 2 : a.comp);
-    const R qline = comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
+    const R qline = mul_rn(comp == 0 ? (R)ix + qo : (R)iy + qo, cell);
     const R q2p = (R)(2 * p);  // (R)(2n) == q2p + (R)(2n - 2p) exactly
     void *psi_b = OUT ? nullptr : (a.psi_list ? a.psi_list[rr] : a.psi);
     void *pos_b = OUT ? a.pos : (a.pos_list ? a.pos_list[rr] : a.pos);
@@ -398,8 +398,8 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
         if (OUT || pos) {
           R q0 = qline, q1 = qline;
           if (comp == 2) {
-            q0 = (q2p + (R)(2 * (n - p)) + qo) * cell;
-            q1 = (q2p + (R)(2 * (n - p) + 1) + qo) * cell;
+            q0 = mul_rn(q2p + (R)(2 * (n - p)) + qo, cell);
+            q1 = mul_rn(q2p + (R)(2 * (n - p) + 1) + qo, cell);
           }
           if constexpr (EXT) {  // Sec. 2.2: periodic shift; gas partners
             pos[n] = C{wrap_box<R>(q0 + sh1 + z.x, box), wrap_box<R>(q1 + sh1 + z.y, box)};

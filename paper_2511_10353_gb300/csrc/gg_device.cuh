@@ -99,6 +99,14 @@ template <typename R> __device__ __forceinline__ R noise_cell(uint64_t seed, uin
   return lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : v[3];
 }
 
+// A product rounded on its own, never fused into an FMA with a later add.
+// Used where the kernels' instantiations differ only in which branches are
+// fixed at compile time (a fused multiply-add in one and not in another
+// would round differently): the lattice coordinates (i + offset) * cell of
+// Eq. 3 and the i m_z factor of the z inverse pass.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Periodic wrap of a coordinate into [0, L) (Eq. 3 positions).
 template <typename R>
 __device__ __forceinline__ R wrap_box(R x, R box) {

@@ -323,7 +323,7 @@ __global__ void k_zinv(const ZInvArgs a) {
     for (int i = 0; i < E; ++i) {
       const int k = p + P * i;
       C v = src[k];
-      if (a.mul_kz) v = C{-(R)k * v.y, (R)k * v.x};  // i m_z, m_z = k for k < N/2
+      if (a.mul_kz) v = C{mul_rn(-(R)k, v.y), mul_rn((R)k, v.x)};  // i m_z, m_z = k for k < N/2
       buf[lay(l, k)] = v;
     }
   }
@@ -349,7 +349,7 @@ __global__ void k_zinv(const ZInvArgs a) {
   const int64_t rr = line / lpr, local = line - rr * lpr;
   const int64_t ix = local / a.n, iy = local - ix * a.n;
   const R box = (R)a.box, cell = (R)a.cell, qo = (R)a.q_offset, vfac = (R)a.vfac;
-  const R qline = a.comp == 0 ? ((R)ix + qo) * cell : ((R)iy + qo) * cell;
+  const R qline = mul_rn(a.comp == 0 ? (R)ix + qo : (R)iy + qo, cell);
   void *psi_b = a.psi_list ? a.psi_list[rr] : a.psi;
   void *pos_b = a.pos_list ? a.pos_list[rr] : a.pos;
   void *vel_b = a.vel_list ? a.vel_list[rr] : a.vel;
@@ -384,8 +384,8 @@ __global__ void k_zinv(const ZInvArgs a) {
     if (pos) {
       R q0 = qline, q1 = qline;
       if (a.comp == 2) {
-        q0 = ((R)(2 * n) + qo) * cell;
-        q1 = ((R)(2 * n + 1) + qo) * cell;
+        q0 = mul_rn((R)(2 * n) + qo, cell);
+        q1 = mul_rn((R)(2 * n + 1) + qo, cell);
       }
       const R sh1 = (R)a.shift, sh2 = (R)a.shift2;  // Sec. 2.2: periodic shift, gas partners
       pos[n] = C{wrap_box<R>(q0 + sh1 + v.x, box), wrap_box<R>(q1 + sh1 + v.y, box)};

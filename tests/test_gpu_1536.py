@@ -11,7 +11,9 @@ this size, so:
   of the GPU FP64 path (which the other tests pin to the oracle at <= 1e-12);
 * the strided passes' tile variants agree bit for bit;
 * Eq. 4's top hat at this size: the planted mode comes out unchanged above
-  the cut and vanishes below it.
+  the cut and vanishes below it;
+* the pos + vel-only path agrees bit for bit with the path that also writes
+  psi.
 """
 import math
 
@@ -173,5 +175,23 @@ def test_merge_cut_planted_mode(gg):
             want = -s * k0[j] / kk ** 2 * np.sin(phase) if r_s * kk >= 1 else 0.0 * phase
             assert np.abs(got - want).max() < 2e-5 * scale, (r_s, j)
     del noise, psi
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def test_pos_vel_only_bit_identical(gg):
+    """The bench's z inverse instantiation (pos + vel only, component fixed
+    at compile time) against the run-time-flag kernel that also writes psi:
+    the same positions and velocities bit for bit, component by component."""
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f32")
+    e = lambda: torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    pos, vel, pos2, vel2, psi = e(), e(), e(), e(), e()
+    for j in range(3):
+        sel = lambda t: [t if c == j else None for c in range(3)]
+        plan.zeldovich(seed=3, out={"psi": [None] * 3, "pos": sel(pos), "vel": sel(vel)})
+        plan.zeldovich(seed=3, out={"psi": sel(psi), "pos": sel(pos2), "vel": sel(vel2)})
+        plan.sync()
+        assert torch.equal(pos, pos2) and torch.equal(vel, vel2), j
+    del pos, vel, pos2, vel2, psi
     plan.close()
     torch.cuda.empty_cache()

@@ -42,3 +42,22 @@ def test_512_matches_oracle(oracle512, prec, tol):
         lim = 4 * float(np.spacing(np.float32(500.0))) if prec == "f32" else 1e-10
         assert np.abs(d).max() < lim + tol * np.abs(oracle512["psi"][j]).max()
         del out, psi
+
+
+def test_512_pos_vel_only_matches_oracle(oracle512):
+    """The bench's launch configuration: all three components, pos + vel
+    only (the compile-time z inverse of the plain path), FP32."""
+    from paper_2511_10353_gb300 import build
+    build.build(verbose=False)
+    import paper_2511_10353_gb300 as gg
+    plan = gg.Plan(512, 500.0, BBKS, 100.0, "f32")
+    plan.autotune(2)
+    out = plan.zeldovich(seed=1, psi=False)
+    plan.sync()
+    lim = 4 * float(np.spacing(np.float32(500.0)))
+    for j in range(3):
+        assert rel_l2(out["vel"][j].cpu().numpy(), oracle512["vel"][j]) < 1e-5
+        d = min_image(out["pos"][j].cpu().numpy().astype(np.float64) - oracle512["pos"][j], 500.0)
+        assert np.abs(d).max() < lim + 1e-5 * np.abs(oracle512["psi"][j]).max()
+    del out
+    plan.close()

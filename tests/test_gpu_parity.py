@@ -141,6 +141,27 @@ def test_partial_outputs_and_corner_lattice(gg):
     _compare(out, ora, box, "f64")
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [24, 64, 192])
+def test_pos_vel_only_outputs(gg, n, prec):
+    """pos + vel without psi (the z inverse instantiation of the plain path,
+    component fixed at compile time): bit-identical to the same outputs of a
+    call that also writes psi (the run-time-flag kernel), and within the
+    parity tolerances of the oracle."""
+    box = 1.25 * n
+    w = dict(n=n, box=box, cosmo=BBKS, z_init=40.0)
+    plan = gg.Plan(n, box, BBKS, 40.0, prec)
+    plain = plan.zeldovich(seed=12, psi=False)
+    full = plan.zeldovich(seed=12)
+    plan.sync()
+    for k in ("pos", "vel"):
+        for j in range(3):
+            assert torch.equal(plain[k][j], full[k][j]), (k, j)
+    ora = run_oracle(w, seed=12)
+    _compare(plain, ora, box, prec, keys=("pos", "vel"))
+    plan.close()
+
+
 def test_planted_mode_closed_form(gg):
     """W(x_n) = cos(k0.x_n): delta = s cos, psi = -s k0/|k0|^2 sin (Eqs. 1-2)."""
     from tests.oracle_cases import cosmology_from
