@@ -251,6 +251,18 @@ def run_batched(args):
                      "peak_source": src},
             "gpu_launches": b.launches() * args.steps, "clocks": clocks}
     b.close()
+    if not args.no_cpu_baseline:  # the oracle on the batch's first two realizations, in turn
+        from oracle.fields import WORKERS
+        secs = cells = 0
+        for w in specs[:2]:
+            t_s, c_s = oracle_sample(w, w["n"])
+            secs += t_s
+            cells += c_s
+        line["cpu_baseline"] = {
+            "value": cells / secs, "unit": "cells/s", "cores": WORKERS, "kind": "oracle",
+            "sample": "realizations 1-2 of the batch (128^3 and 192^3, seeds 1-2), one after "
+                      "the other, FP64 numpy/scipy; FFTs on %d scipy workers; %.1f s"
+                      % (WORKERS, secs)}
     print(json.dumps(line), flush=True)
 
 
