@@ -310,8 +310,8 @@ __device__ __forceinline__ void inverse_head_store(int p, const Cx<R> *v, const 
 
 // ------------------------------------------------------------ tile policy
 // Tile variants the autotuner chooses between (V = 0, 1, 2 for the strided
-// pass; V = 0, 1 for the z passes). An invalid variant for a size falls back
-// to variant 0's shape.
+// pass; V = 0 .. 3 for the z passes). An invalid variant for a size falls
+// back to variant 0's shape.
 //
 // Strided pass, variant
 //   0: E = lcm of the radices, rows of up to 128 bytes, <= 512 threads
