@@ -1177,6 +1177,7 @@ gg_status group_passes(gg_batch::Group &g, cudaStream_t s, uint32_t sig) {
       zi.psi_list = ((sig >> (0 * 3 + j)) & 1) ? g.d_lists + (0 * 3 + j) * nb : nullptr;
       zi.pos_list = ((sig >> (1 * 3 + j)) & 1) ? g.d_lists + (1 * 3 + j) * nb : nullptr;
       zi.vel_list = ((sig >> (2 * 3 + j)) & 1) ? g.d_lists + (2 * 3 + j) * nb : nullptr;
+      zi.lists_full = ((sig >> (9 + 1 * 3 + j)) & 1) && ((sig >> (9 + 2 * 3 + j)) & 1);
       zi.n = n;
       zi.lines_per_cta = plan->z_lines;
       zi.comp = j;
@@ -1722,14 +1723,19 @@ gg_status gg_batch_run(gg_batch_t *b, const uint64_t *seeds, void *const *psi, v
   if (b->ran && (e = cudaEventSynchronize(b->done)) != cudaSuccess)  // staging is re-read by the graph
     return cuda_fail(nullptr, e, "waiting for the previous batch run");
   void *const *outs[3] = {psi, pos, vel};
-  uint32_t sig = 0;
+  // bits 0-8: (output o, component j) wanted by some realization; bits 9-17:
+  // wanted by every realization (the graph's kernels may then skip the
+  // per-realization null checks)
+  uint32_t sig = 0, all = (1u << 9) - 1;
   for (int i = 0; i < b->count; ++i)
     for (int o = 0; o < 3; ++o)
       for (int j = 0; j < 3; ++j) {
         const void *ptr = outs[o] ? outs[o][3 * i + j] : nullptr;
         if (ptr && ((uintptr_t)ptr & 15u)) return fail(nullptr, GG_EINVAL, "output buffer unaligned");
         if (ptr) sig |= 1u << (o * 3 + j);
+        else all &= ~(1u << (o * 3 + j));
       }
+  sig |= all << 9;
   for (auto &g : b->groups) {
     const int nb = (int)g.members.size();
     for (int k = 0; k < nb; ++k) {

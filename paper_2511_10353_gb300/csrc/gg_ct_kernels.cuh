@@ -274,8 +274,8 @@ template <int LD, int PAD> __device__ __forceinline__ int zpad(int l, int n) {
 // pos2), compiled only into the extended instantiation.
 // OUT: 0 reads the outputs and the component from the arguments; kZPosVel
 // (x or y component) and kZPosVelZ (z component, i m_z) fix the plain
-// path's pos + vel outputs at compile time (no psi, no accumulation, no
-// per-realization pointer lists).
+// path's pos + vel outputs at compile time (no psi, no accumulation; with
+// per-realization lists, every entry set).
 constexpr int kZPosVel = 1, kZPosVelZ = 2;
 template <typename R, int N, int V, bool EXT = false, int OUT = 0>
 __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_INV)
@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     const R qline = mul_rn(comp == 0 ? (R)ix + qo : (R)iy + qo, cell);
     const R q2p = (R)(2 * p);  // (R)(2n) == q2p + (R)(2n - 2p) exactly
     void *psi_b = OUT ? nullptr : (a.psi_list ? a.psi_list[rr] : a.psi);
-    void *pos_b = OUT ? a.pos : (a.pos_list ? a.pos_list[rr] : a.pos);
-    void *vel_b = OUT ? a.vel : (a.vel_list ? a.vel_list[rr] : a.vel);
-    const int64_t off = (int64_t)((!OUT && (a.psi_list || a.pos_list || a.vel_list)) ? local : line) * M;
+    void *pos_b = a.pos_list ? a.pos_list[rr] : a.pos;
+    void *vel_b = a.vel_list ? a.vel_list[rr] : a.vel;
+    const int64_t off = (int64_t)(((!OUT && a.psi_list) || a.pos_list || a.vel_list) ? local : line) * M;
     C *psi = psi_b ? reinterpret_cast<C *>(psi_b) + off : nullptr;
     C *pos = pos_b ? reinterpret_cast<C *>(pos_b) + off : nullptr;
     C *vel = vel_b ? reinterpret_cast<C *>(vel_b) + off : nullptr;
@@ -569,8 +569,11 @@ template <typename R, int... NS> struct CtTable {
     return e;
   }
   template <int N, int V> static cudaError_t zinv_v(const ZInvArgs &a, cudaStream_t s) {
-    const bool plain = !a.psi && a.pos && a.vel && !a.accumulate && !a.psi_list && !a.pos_list &&
-                       !a.vel_list && (a.mul_kz != 0) == (a.comp == 2);
+    const bool lists = a.pos_list || a.vel_list;
+    const bool outs = lists ? a.pos_list && a.vel_list && a.lists_full && !a.pos && !a.vel
+                            : a.pos && a.vel;
+    const bool plain = !a.psi && !a.psi_list && !a.accumulate && outs &&
+                       (a.mul_kz != 0) == (a.comp == 2);
     if (!plain) return ct_launch_zinv<R, N, V>(a, s);
     return a.comp == 2 ? ct_launch_zinv<R, N, V, false, kZPosVelZ>(a, s)
                        : ct_launch_zinv<R, N, V, false, kZPosVel>(a, s);

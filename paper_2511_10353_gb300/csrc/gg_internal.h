@@ -124,6 +124,7 @@ struct ZInvArgs {
   void *const *psi_list;  // batched form: device arrays of per-realization outputs
   void *const *pos_list;  // (entries may be null); when set they replace psi/pos/vel
   void *const *vel_list;
+  int lists_full;         // every entry of pos_list and vel_list is set (batched form)
   // Sec. 2.4 merge: a coarse periodic grid of n_low^3 reals (cell-centred)
   // whose cloud-in-cell interpolation to this grid's cell centres is added to
   // the transform's output before the epilogue; nullptr: none
