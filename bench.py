@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-north-star", action="store_true",
+                    help="skip the 1536^3 leg of the default run")
     ap.add_argument("--variants", default=None,
                     help="comma list of 6 tile variants instead of autotuning (profiling runs)")
     return ap.parse_args()
@@ -167,10 +169,13 @@ def oracle_sample(w, n_s):
 def cpu_baseline(w, n_s=256):
     from oracle.fields import WORKERS
     secs, cells = oracle_sample(w, n_s)
+    what = ("one step of the workload itself (%d^3, box %.1f Mpc/h, seed %d)" % (n_s, w["box"], w["seed"])
+            if n_s == w["n"] else
+            "one %d^3 realization (box %.1f Mpc/h, same cell size and cosmology)"
+            % (n_s, w["box"] * n_s / w["n"]))
     return {"value": cells / secs, "unit": "cells/s", "cores": WORKERS, "kind": "oracle",
-            "sample": "one %d^3 realization (box %.1f Mpc/h, same cell size and cosmology), "
-                      "FP64 numpy/scipy; noise single-threaded, FFTs on %d scipy workers; %.1f s"
-                      % (n_s, w["box"] * n_s / w["n"], WORKERS, secs)}
+            "sample": what + ", all three components' psi, pos and vel, FP64 numpy/scipy; "
+                      "noise single-threaded, FFTs on %d scipy workers; %.1f s" % (WORKERS, secs)}
 
 
 def run_reference(args, w):
@@ -440,6 +445,146 @@ def run_features(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def time_plain(gg, w, steps, warmup, variants_arg, world, barrier, gpu_id, allreduce_max):
+    """Plan, autotune, warm-up, then `steps` timed steps of noise -> pos + vel
+    (CUDA events on the plan's stream, per-kernel events on the same stream,
+    clocks sampled meanwhile). Returns (result dict, plan, variants)."""
+    import torch
+    n = w["n"]
+    cells = n ** 3
+    plan = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], w["prec"])
+    shape = (n, n, n)
+    out = {"psi": [None] * 3,
+           "pos": [torch.empty(shape, dtype=plan.dtype, device="cuda") for _ in range(3)],
+           "vel": [torch.empty(shape, dtype=plan.dtype, device="cuda") for _ in range(3)]}
+    stream = torch.cuda.current_stream()
+    t_tune = time.perf_counter()
+    if variants_arg:
+        plan.set_variants([int(v) for v in variants_arg.split(",")])
+        variants = plan.variants()
+    else:
+        variants = plan.autotune(3)  # tile variants per pass, timed on this plan's buffers
+    t_tune = time.perf_counter() - t_tune
+    for i in range(max(3, warmup)):
+        plan.zeldovich(seed=1 + i, out=out)
+    plan.sync()
+    plan.set_profiling(True)
+    plan.profile(reset=True)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        plan.zeldovich(seed=1 + i, out=out)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    plan.sync()
+    prof = plan.profile(reset=True)
+    plan.set_profiling(False)
+    ms = allreduce_max(t0.elapsed_time(t1))
+    value = world * cells * steps / (ms * 1e-3)
+    launches = sum(v["launches"] for v in prof.values())
+    peak, peak_src = peak_hbm()
+    kernels = {}
+    for name, v in prof.items():
+        per = v["ms"] / v["launches"]
+        gbs = v["bytes"] / (per * 1e-3) / 1e9
+        kernels[name] = {"ms_per_launch": per, "launches": v["launches"], "GB_s": gbs,
+                         "frac_of_peak": gbs / peak,
+                         "share": v["ms"] / sum(x["ms"] for x in prof.values())}
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dper = prof[dom]["ms"] / prof[dom]["launches"]
+    achieved = prof[dom]["bytes"] / (dper * 1e-3) / 1e9
+    traffic = None
+    rec = NCU_TRAFFIC.get((dom, config_of(w)["workload"]))
+    if rec and rec[1] == kernel_source_hash():
+        traffic = rec[0]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": prof[dom]["bytes"], "traffic": traffic}
+    step_bytes = sum(v["bytes"] * v["launches"] for v in prof.values()) / steps
+    path_gbs = step_bytes / (ms / steps * 1e-3) / 1e9
+    res = {"value": value, "ms_per_step": ms / steps, "steps": steps,
+           "config": dict(config_of(w), tile_variants=variants, autotune_s=round(t_tune, 3)),
+           "roofline": roofline,
+           "path": {"algorithmic_bytes_per_cell": step_bytes / cells, "GB_s": path_gbs,
+                    "frac_of_peak": path_gbs / peak},
+           "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
+    del out
+    torch.cuda.empty_cache()
+    return res, plan, variants
+
+
+def fp64_leg(gg, w, plan, value_per_gpu, steps):
+    """The FP64 plain path on the same workload: the FP32 psi's relative L2
+    error against it, and its own rate. Closes the FP32 plan (its workspaces
+    make room for the FP64 grids: 261 GB at 1536^3)."""
+    import torch
+    n = w["n"]
+    cells = n ** 3
+    shape = (n, n, n)
+    plan64 = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], "f64")
+    psi64 = torch.empty(shape, dtype=torch.float64, device="cuda")
+    psi32 = torch.empty(shape, dtype=torch.float32, device="cuda")
+    errs = []
+    for j in range(3):
+        sel = lambda t: {"psi": [t if c == j else None for c in range(3)], "pos": [None] * 3,
+                         "vel": [None] * 3}
+        plan64.zeldovich(seed=1, out=sel(psi64))
+        plan.zeldovich(seed=1, out=sel(psi32))
+        torch.cuda.synchronize()
+        num = den = 0.0
+        for x0 in range(0, n, 128):  # slabs bound the FP64 temporaries
+            d = psi32[x0:x0 + 128].double() - psi64[x0:x0 + 128]
+            num += float((d * d).sum())
+            den += float((psi64[x0:x0 + 128] ** 2).sum())
+        errs.append(math.sqrt(num / den))
+    del psi64, psi32
+    err = {"psi_rel_l2": errs, "reference": "GPU FP64 path (within 1e-12 of the FP64 oracle "
+           "in tests/test_gpu_fullsize.py, 1e-11 of the oracle's closed form at 1536^3 in "
+           "tests/test_gpu_1536.py)"}
+    plan.close()
+    torch.cuda.empty_cache()
+    need = 6 * cells * 8 + (1 << 30)
+    out64, why = None, None
+    if torch.cuda.mem_get_info()[0] >= need:
+        out64 = {"psi": [None] * 3,
+                 "pos": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)],
+                 "vel": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)]}
+        try:  # the plan's own workspaces may still not fit: GG_ENOMEM, nothing launched
+            plan64.zeldovich(seed=1, out=out64)
+            torch.cuda.synchronize()
+        except gg.GGError as ex:
+            out64, why = None, str(ex)
+    else:
+        why = "FP64 pos + vel grids (%.0f GB) do not fit in device memory" % (need / 1e9)
+    if out64 is not None:
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            plan64.zeldovich(seed=1 + i, out=out64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / steps
+        v64 = cells / (ms64 * 1e-3)
+        fp64 = {"value": v64, "unit": "cells/s", "ms_per_step": ms64, "steps": steps,
+                "fp32_speedup": value_per_gpu / v64}
+        del out64
+    else:
+        fp64 = {"skipped": why}
+    plan64.close()
+    del plan64
+    torch.cuda.empty_cache()
+    return err, fp64
+
+
 def main():
     args = parse()
     if args.workload == "batched_48" and args.impl == "ours":
@@ -481,146 +626,38 @@ def main():
         if dist:
             dist.barrier()
 
-    n = w["n"]
-    cells = n ** 3
-    plan = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], w["prec"])
-    dt = plan.dtype
-    shape = (n, n, n)
-    out = {"psi": [None] * 3,
-           "pos": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)],
-           "vel": [torch.empty(shape, dtype=dt, device="cuda") for _ in range(3)]}
-    stream = torch.cuda.current_stream()
-    t_tune = time.perf_counter()
-    if args.variants:
-        plan.set_variants([int(v) for v in args.variants.split(",")])
-        variants = plan.variants()
-    else:
-        variants = plan.autotune(3)  # tile variants per pass, timed on this plan's buffers
-    t_tune = time.perf_counter() - t_tune
-    for i in range(max(3, args.warmup)):
-        plan.zeldovich(seed=1 + i, out=out)
-    plan.sync()
-    # timed region: K steps, per-kernel events on the plan's (= current) stream
-    plan.set_profiling(True)
-    plan.profile(reset=True)
+    def allreduce_max(x):
+        if not dist:
+            return x
+        tt = torch.tensor([x], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
     dev_props = torch.cuda.get_device_properties(torch.cuda.current_device())
     gpu_id = "GPU-" + str(dev_props.uuid) if getattr(dev_props, "uuid", None) else str(local_rank)
-    sampler = ClockSampler(gpu_id)
-    sampler.start()
-    barrier()
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(args.steps):
-        plan.zeldovich(seed=1 + i, out=out)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    plan.sync()
-    prof = plan.profile(reset=True)
-    plan.set_profiling(False)
-    ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * cells * args.steps / (ms * 1e-3)
-    launches = sum(v["launches"] for v in prof.values())
-
-    peak, peak_src = peak_hbm()
-    kernels = {}
-    for name, v in prof.items():
-        per = v["ms"] / v["launches"]
-        gbs = v["bytes"] / (per * 1e-3) / 1e9
-        kernels[name] = {"ms_per_launch": per, "launches": v["launches"], "GB_s": gbs,
-                         "share": v["ms"] / sum(x["ms"] for x in prof.values())}
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    dper = prof[dom]["ms"] / prof[dom]["launches"]
-    achieved = prof[dom]["bytes"] / (dper * 1e-3) / 1e9
-    traffic = None
-    rec = NCU_TRAFFIC.get((dom, args.workload))
-    if rec and rec[1] == kernel_source_hash():
-        traffic = rec[0]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": prof[dom]["bytes"], "traffic": traffic}
-    step_bytes = sum(v["bytes"] * v["launches"] for v in prof.values()) / args.steps
-    path_gbs = step_bytes / (ms / args.steps * 1e-3) / 1e9
-
+    n = w["n"]
+    cells = n ** 3
+    res, plan, variants = time_plain(gg, w, args.steps, args.warmup, args.variants, world,
+                                     barrier, gpu_id, allreduce_max)
+    value = res["value"]
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if w["prec"] == "f32" else "f64", "data": "synthetic",
-            "config": dict(config_of(w), tile_variants=variants, autotune_s=round(t_tune, 3)),
-            "roofline": roofline,
-            "path": {"algorithmic_bytes_per_cell": step_bytes / cells, "GB_s": path_gbs,
-                     "frac_of_peak": path_gbs / peak},
-            "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
-    del out
-    torch.cuda.empty_cache()
+            "dtype": "f32" if w["prec"] == "f32" else "f64", "data": "synthetic"}
+    line.update({k: res[k] for k in ("config", "roofline", "path", "kernels", "gpu_launches",
+                                     "clocks")})
 
     # FP64 plain path on the same workload, and the FP32 error against it
     if not args.no_fp64 and w["prec"] == "f32":
-        plan64 = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], "f64")
         k64 = max(2, min(10, args.steps // 10))
-        psi64 = torch.empty(shape, dtype=torch.float64, device="cuda")
-        psi32 = torch.empty(shape, dtype=torch.float32, device="cuda")
-        errs = []
-        for j in range(3):
-            o64 = {"psi": [psi64 if c == j else None for c in range(3)], "pos": [None] * 3,
-                   "vel": [None] * 3}
-            o32 = {"psi": [psi32 if c == j else None for c in range(3)], "pos": [None] * 3,
-                   "vel": [None] * 3}
-            plan64.zeldovich(seed=1, out=o64)
-            plan.zeldovich(seed=1, out=o32)
-            torch.cuda.synchronize()
-            errs.append(float(torch.linalg.vector_norm(psi32.double() - psi64)
-                              / torch.linalg.vector_norm(psi64)))
-        del psi64, psi32, o64, o32
-        line["err_vs_fp64"] = {"psi_rel_l2": errs, "reference": "GPU FP64 path (within 1e-12 "
-                               "of the FP64 oracle in tests/test_gpu_fullsize.py)"}
-        # the FP32 plan's workspaces make room for the FP64 pos + vel grids
-        # (174 GB at 1536^3); it is re-made for the end-to-end leg
-        plan.close()
+        line["err_vs_fp64"], line["fp64"] = fp64_leg(gg, w, plan, value / world, k64)
         plan = None
-        torch.cuda.empty_cache()
-        need = 6 * cells * 8 + (1 << 30)
-        out64, why = None, None
-        if torch.cuda.mem_get_info()[0] >= need:
-            out64 = {"psi": [None] * 3,
-                     "pos": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)],
-                     "vel": [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)]}
-            try:  # the plan's own workspaces may still not fit: GG_ENOMEM, nothing launched
-                plan64.zeldovich(seed=1, out=out64)
-                torch.cuda.synchronize()
-            except gg.GGError as ex:
-                out64, why = None, str(ex)
-        else:
-            why = "FP64 pos + vel grids (%.0f GB) do not fit in device memory" % (need / 1e9)
-        if out64 is not None:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for i in range(k64):
-                plan64.zeldovich(seed=1 + i, out=out64)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms64 = e0.elapsed_time(e1) / k64
-            v64 = cells / (ms64 * 1e-3)
-            line["fp64"] = {"value": v64, "unit": "cells/s", "ms_per_step": ms64, "steps": k64,
-                            "fp32_speedup": (value / world) / v64}
-            del out64
-        else:
-            line["fp64"] = {"skipped": why}
-        plan64.close()
-        del plan64
-        torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: caller white noise
     # (the paper's "WN from file" input) up, positions and velocities down
     if not args.no_e2e:
+        dt = torch.float32 if w["prec"] == "f32" else torch.float64
+        shape = (n, n, n)
         if plan is None:
             plan = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], w["prec"])
             plan.set_variants(variants)
@@ -628,17 +665,13 @@ def main():
         hout = {"psi": [None] * 3,
                 "pos": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)],
                 "vel": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)]}
-        ke = max(2, min(8, args.steps // 10))
+        ke = max(5, min(10, args.steps // 4))
         plan.zeldovich_host(noise=hn, out=hout)
         barrier()
         t = time.perf_counter()
         for i in range(ke):
             plan.zeldovich_host(noise=hn, out=hout)
-        el = time.perf_counter() - t
-        if dist:
-            tt = torch.tensor([el], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = allreduce_max(time.perf_counter() - t)
         esz = torch.finfo(dt).bits // 8
         # the copy engines' rates on the same pinned buffers, for scale: the
         # step's outputs are written by the kernels themselves over the host
@@ -662,12 +695,34 @@ def main():
         line["e2e"] = {"value": world * cells * ke / el, "unit": "cells/s", "steps": ke,
                        "h2d_bytes_per_step": cells * esz, "d2h_bytes_per_step": 6 * cells * esz,
                        "api": "gg_zeldovich_host (pinned host noise in, pos/vel out)",
+                       "timing": "host wall clock over the steps (each call synchronous)",
                        "copy_GB_s": rates, "copy_time_over_step_time": bound_s / (el / ke)}
-
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        del hn, hout
     if plan is not None:
         plan.close()
+        plan = None
+    torch.cuda.empty_cache()
+
+    # the 1536^3 precision workload (EH no-wiggle, 2000 Mpc/h), timed in the
+    # same run when the headline workload is the default 512^3 one
+    if args.workload == "zeldovich_512_fp32" and not args.no_north_star:
+        w2 = dict(WORKLOADS["zeldovich_1536_fp32"])
+        k2 = max(10, min(20, args.steps))
+        res2, plan2, _ = time_plain(gg, w2, k2, min(args.warmup, 3), None, world, barrier,
+                                    gpu_id, allreduce_max)
+        ns = {"workload": "zeldovich_1536_fp32", "unit": "cells/s"}
+        ns.update(res2)
+        if not args.no_fp64:
+            ns["err_vs_fp64"], ns["fp64"] = fp64_leg(gg, w2, plan2, res2["value"] / world, 2)
+        else:
+            plan2.close()
+        del plan2
+        torch.cuda.empty_cache()
+        line["north_star_1536"] = ns
+        line["gpu_launches"] += res2["gpu_launches"]
+
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, n_s=min(n, 512))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -32,9 +32,9 @@
  *
  * Asynchrony: compute calls enqueue work on the plan's stream and return at
  * once. Argument errors return GG_EINVAL before anything is enqueued. Launch
- * errors return GG_ECUDA. Errors detected on the device (an exceeded wait
- * budget, a bounds violation in a checking build) are latched in a device
- * word and returned by the next gg_sync().
+ * errors return GG_ECUDA. The one error detected on the device, a tile-copy
+ * wait that gave up (GG_ETIMEOUT, after two seconds), is latched in a device
+ * word and returned by the next gg_sync(), which clears it.
  *
  * Thread safety: a plan may be used by one host thread at a time. Distinct
  * plans are independent.
@@ -54,8 +54,7 @@ typedef enum {
   GG_EINVAL = -1,   /* invalid argument; nothing enqueued */
   GG_ENOMEM = -2,   /* device or host allocation failed */
   GG_ECUDA = -3,    /* a CUDA runtime call or a kernel launch failed */
-  GG_ETIMEOUT = -4, /* a bounded device-side wait gave up */
-  GG_EDEVICE = -5   /* the device reported an error (bounds check) */
+  GG_ETIMEOUT = -4  /* a bounded device-side wait gave up */
 } gg_status;
 
 typedef enum { GG_F32 = 0, GG_F64 = 1 } gg_prec;
@@ -272,10 +271,14 @@ void gg_batch_free(gg_batch_t *batch);
  * both 16-byte aligned device memory; `stream` is a cudaStream_t (NULL = the
  * legacy default stream). Synchronous: returns after the result is written.
  *
- * All calls on one device share those arrays: calls whose work overlaps on
- * the GPU race and corrupt each other's results, so serialise them. The
- * first call on each device sets the arrays' device addresses up (it may load
- * the library's device code); make it before any stream capture.
+ * All calls on one device from any stream or host thread of the process
+ * share those arrays: calls whose work overlaps on the GPU race and corrupt
+ * each other's results, so serialise them. The first call on each device
+ * looks the arrays' device addresses up (it may load the library's device
+ * code) and keeps them for the life of the process: cudaDeviceReset between
+ * calls is not supported. The call copies host-made tables with
+ * cudaMemcpyAsync from host stack memory and synchronises its stream before
+ * returning, so it cannot be called while its stream is being captured.
  * n > GG_STATIC_MAX_N returns GG_EINVAL with a message in gg_last_error(NULL);
  * invalid parameters as in gg_plan. */
 gg_status gg_gaussian_field_static(const gg_params *p, uint64_t seed, const void *noise_dev,
@@ -429,8 +432,21 @@ gg_status gg_refine_dims(const gg_refine_params *p, int64_t dims[3]);
 gg_status gg_refine_noise(const gg_refine_params *p, const void *parent_dev, uint64_t seed_child,
                           void *child_dev, void *stream);
 
-/* Wait for the plan's stream; return the first latched device error, if any. */
+/* Wait for the plan's stream; return the first latched device error, if any
+ * (GG_ETIMEOUT), and clear it. */
 gg_status gg_sync(gg_plan_t *plan);
+
+/* Fault test of the device-side waits (no paper counterpart; off unless
+ * armed). kind GG_TEST_SKIP_COPY makes the next y forward pass of the plan
+ * issue none of its tile copies: every CTA's first copy wait gives up after
+ * wait_us microseconds (1 <= wait_us <= 1000000), the CTA returns, the rest
+ * of the call runs on whatever the workspace holds (its outputs are
+ * meaningless) and the next gg_sync() returns GG_ETIMEOUT. The fault applies
+ * to that one launch only; later calls on the plan run normally. kind
+ * GG_TEST_NONE disarms. No GPU fault, trap or unbounded wait is involved. */
+#define GG_TEST_NONE 0
+#define GG_TEST_SKIP_COPY 1
+gg_status gg_test_arm_fault(gg_plan_t *plan, int kind, uint32_t wait_us);
 
 /* Message of the last failed call on this plan (plan = NULL: of the last
  * failed call on this host thread that had no plan). Never NULL. */

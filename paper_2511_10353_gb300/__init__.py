@@ -25,12 +25,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libgg.so")
 _lib = None
 
-GG_OK, GG_EINVAL, GG_ENOMEM, GG_ECUDA, GG_ETIMEOUT, GG_EDEVICE = 0, -1, -2, -3, -4, -5
+GG_OK, GG_EINVAL, GG_ENOMEM, GG_ECUDA, GG_ETIMEOUT = 0, -1, -2, -3, -4
+GG_TEST_NONE, GG_TEST_SKIP_COPY = 0, 1
 GG_F32, GG_F64 = 0, 1
 TF = {"bbks": 0, "eh_nw": 1, "table": 2}
 GG_Q_CORNER = 0x1
 _STATUS = {GG_EINVAL: "GG_EINVAL", GG_ENOMEM: "GG_ENOMEM", GG_ECUDA: "GG_ECUDA",
-           GG_ETIMEOUT: "GG_ETIMEOUT", GG_EDEVICE: "GG_EDEVICE"}
+           GG_ETIMEOUT: "GG_ETIMEOUT"}
 
 
 class GGError(RuntimeError):
@@ -136,6 +137,7 @@ _SIGS = {
     "gg_refine_noise": (ctypes.c_int, [ctypes.POINTER(RefineParams), ctypes.c_void_p, ctypes.c_uint64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "gg_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "gg_test_arm_fault": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]),
     "gg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gg_free": (None, [ctypes.c_void_p]),
 }
@@ -473,6 +475,12 @@ class Plan:
 
     def sync(self):
         _check(lib().gg_sync(self._h), self._h)
+
+    def arm_fault(self, kind="skip_copy", wait_us=2000):
+        """Fault test: the next y forward pass issues no tile copies, so its
+        waits give up after wait_us and the next sync raises GG_ETIMEOUT."""
+        k = {"none": GG_TEST_NONE, "skip_copy": GG_TEST_SKIP_COPY}[kind]
+        _check(lib().gg_test_arm_fault(self._h, k, int(wait_us)), self._h)
 
     # ------------------------------------------------------- adjoint form
     def _ptrs3(self, ts):

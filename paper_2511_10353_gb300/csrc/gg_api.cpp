@@ -67,6 +67,9 @@ struct gg_plan {
   // 0 z forward, 1 y forward, 2 x fused, 3 y inverse (x branch),
   // 4 y inverse (y/z branches), 5 z inverse
   int variant[6] = {0, 0, 0, 0, 0, 0};
+  // fault test (gg_test_arm_fault): the next y forward pass issues no copies
+  int test_skip_copy = 0;
+  uint32_t test_wait_us = 0;
   std::string last_error;
   // host-buffer entry point: device staging of two components, a copy stream
   void *stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -314,17 +317,7 @@ template <typename R>
 void choose_tiles(gg_plan_t *plan) {
   const int n = (int)plan->p.n, half = n / 2;
   const size_t cb = 2 * sizeof(R);
-  const size_t smem_cap = 110 * 1024;
-  // z passes: about 256 threads per CTA
-  {
-    const int P = half / plan->st_half.e;
-    int cap = std::min(gg::max_block_threads_z<R>(0, plan->st_half.e),
-                       gg::max_block_threads_z<R>(2, plan->st_half.e));
-    if (cap <= 0) cap = 256;
-    int lines = std::max(1, 256 / P);
-    while (lines > 1 && (P * lines > cap || gg::zpass_smem_bytes(half, lines, cb) > smem_cap)) lines /= 2;
-    plan->z_lines = lines;
-  }
+  plan->z_lines = gg::z_lines_per_cta<R>(plan->st_half);
   // strided passes: rows of up to 128 bytes, halved while two tiles would not
   // fit in shared memory or the CTA would exceed 512 threads (or what the
   // kernel's registers allow); TMA unless FP32 rows of N/2 complex values are
@@ -463,6 +456,11 @@ gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
   c.dst[0] = plan->work;
   c.mul[0] = gg::kMulNone;
   c.variant = plan->variant[1];
+  if (plan->test_skip_copy) {  // armed fault test: this launch only
+    c.test_skip_copy = 1;
+    c.wait_us = plan->test_wait_us;
+    plan->test_skip_copy = 0;
+  }
   return launch_axis_timed<R>(plan, c, kYFwd, "y forward pass");
 }
 
@@ -1222,6 +1220,34 @@ void batch_release(gg_batch_t *b) {
 
 namespace gg {
 
+template <typename R>
+int z_lines_per_cta(const FftStages &st_half) {
+  const int half = st_half.len, P = half / st_half.e;
+  const size_t cb = 2 * sizeof(R), smem_cap = 110 * 1024;
+  int cap = std::min(max_block_threads_z<R>(0, st_half.e), max_block_threads_z<R>(2, st_half.e));
+  if (cap <= 0) cap = 256;
+  int lines = std::max(1, 256 / P);
+  while (lines > 1 && (P * lines > cap || zpass_smem_bytes(half, lines, cb) > smem_cap)) lines /= 2;
+  return lines;
+}
+template int z_lines_per_cta<float>(const FftStages &);
+template int z_lines_per_cta<double>(const FftStages &);
+
+bool info_and_filter(const gg_params *p, gg_info *info, double *s, int64_t count, const char **msg) {
+  thread_local std::string why;
+  why = validate(p);
+  if (!why.empty()) {
+    if (msg) *msg = why.c_str();
+    return false;
+  }
+  const cosmo::Model m = make_model(p);
+  std::memset(info, 0, sizeof(*info));
+  fill_info(p, m, info);
+  info->workspace_bytes = (int64_t)workspace_bytes(p);
+  filter_values(p, m, info->growth, s, count);
+  return true;
+}
+
 bool make_stages(int len, FftStages *st) {
   std::memset(st, 0, sizeof(*st));
   if (len < 1) return false;
@@ -1631,9 +1657,23 @@ gg_status gg_sync(gg_plan_t *plan) {
   if (e != cudaSuccess) return cuda_fail(plan, e, "reading the device error word");
   if (word == 0) return GG_OK;
   cudaMemset(plan->err, 0, sizeof(int));
+  if (word == 2) return fail(plan, GG_ETIMEOUT, "a device-side tile-copy wait gave up");
   char msg[96];
-  std::snprintf(msg, sizeof msg, "device reported error code %d", word);
-  return fail(plan, word == 2 ? GG_ETIMEOUT : GG_EDEVICE, msg);
+  std::snprintf(msg, sizeof msg, "unexpected device error word %d", word);
+  return fail(plan, GG_ECUDA, msg);
+}
+
+gg_status gg_test_arm_fault(gg_plan_t *plan, int kind, uint32_t wait_us) {
+  if (!plan) return fail(nullptr, GG_EINVAL, "plan is NULL");
+  if (kind == GG_TEST_NONE) {
+    plan->test_skip_copy = 0;
+    return GG_OK;
+  }
+  if (kind != GG_TEST_SKIP_COPY) return fail(plan, GG_EINVAL, "unknown fault kind");
+  if (wait_us < 1 || wait_us > 1000000) return fail(plan, GG_EINVAL, "wait_us must be in [1, 1e6]");
+  plan->test_skip_copy = 1;
+  plan->test_wait_us = wait_us;
+  return GG_OK;
 }
 
 const char *gg_last_error(const gg_plan_t *plan) {

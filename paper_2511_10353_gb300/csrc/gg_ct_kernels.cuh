@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     const int64_t outer = tt / INNER;
     const int chunk = (int)(tt - outer * INNER);
     C *dst = bufs + sb * TILE_STRIDE;
+    if (a.test_skip_copy) return;  // fault test: the wait for this tile runs out
     mbar_arrive_expect_tx(&bars[sb], (uint32_t)(TILE * sizeof(C)));
 #pragma unroll
     for (int i = 0; i < N; i += Pol::ROWS_BOX) {
@@ -122,10 +123,10 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
           if (q >= 0) prefetch_l1(table + q);
         }
     }
-    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], phase, a.err));
+    const bool ok = __syncthreads_and(mbar_wait(&bars[sb], phase, a.err, a.wait_us));
     if (!ok) {  // late: no other copy is in flight
-      if (tid == 0 && tn < ntiles && !late)
-        mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+      if (tid == 0 && tn < ntiles && !late && !a.test_skip_copy)
+        mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr, a.wait_us);
       return;
     }
     auto ld_smem = [&](int n) { return buf[n * B + c]; };

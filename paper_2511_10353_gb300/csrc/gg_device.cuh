@@ -279,13 +279,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity. Returns false (and sets
-// *err = 2) when the budget of polls runs out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
-  for (uint32_t i = 0; i < (1u << 24); ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicExch(err, 2);
-  return false;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity: gives up after limit_us
+// microseconds of the global timer (0: two seconds, far beyond any tile
+// copy), then returns false and sets *err = 2 (GG_ETIMEOUT on the host).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          uint32_t limit_us = 0) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  const uint64_t lim = 1000ull * (limit_us ? limit_us : 2000000u);
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > lim) {
+      if (err) atomicExch(err, 2);
+      return false;
+    }
+  return true;
 }
 // 3-D tiled TMA load global -> shared, completion counted on `bar`.
 __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t *bar, int c0, int c1,

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "gg.h"
+
 namespace gg {
 
 constexpr int kMaxStages = 16;
@@ -78,6 +80,10 @@ struct AxisArgs {
   int nbatch;             // realizations in the buffers (<= 0 means 1), outermost
   int64_t batch_stride;   // complex elements between realizations
   int qmin;               // with pre: modes with m2 < qmin get 0 (Eq. 4 top hat; 0: none)
+  // fault test (gg_test_arm_fault): no tile copy is issued, so every CTA's
+  // first wait gives up after wait_us and reports GG_ETIMEOUT; 0 normally
+  int test_skip_copy;
+  uint32_t wait_us;       // limit of the copy waits in microseconds (0: the default)
 };
 
 // Forward z pass: real lines of N (generated noise or caller noise) -> half
@@ -226,5 +232,14 @@ cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint3
 // Shared-memory bytes of one CTA of each pass (the host sizes tiles with these).
 size_t zpass_smem_bytes(int half_len, int lines, size_t complex_bytes);
 size_t axis_smem_bytes(int len, int cols, size_t complex_bytes);
+// Lines per CTA of the run-time z passes (forward and inverse) for lines of
+// st_half.len complex points: about 256 threads, halved while the CTA would
+// exceed the register cap of either kernel or the shared-memory limit.
+template <typename R> int z_lines_per_cta(const FftStages &st_half);
+// The FP64 cosmology of *p (growth, velocity factor, ...) and the Eq. 1
+// filter S(m2) = D sqrt(P(k)/V) for m2 < count, from one evaluation of the
+// model (its sigma_8 and growth integrals). Returns false with *msg set when
+// *p is invalid.
+bool info_and_filter(const gg_params *p, gg_info *info, double *s, int64_t count, const char **msg);
 
 }  // namespace gg

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
     const int64_t outer = tt / a.inner_chunks;
     const int chunk = (int)(tt - outer * a.inner_chunks);
     C *dst = bufs + sb * stride_elems;
+    if (a.test_skip_copy) return;  // fault test: the wait for this tile runs out
     mbar_arrive_expect_tx(&bars[sb], tile_bytes);
     const int c0 = chunk * B * 2;  // innermost coordinate in reals
     for (int i = 0; i < N; i += a.rows_box) {
@@ -212,10 +213,11 @@ __global__ void __launch_bounds__(E >= 24 ? 256 : 512, 1)
       });
     }
     if (use_tma) {
-      const bool ok = __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err));
+      const bool ok =
+          __syncthreads_and(mbar_wait(&bars[sb], (uint32_t)((it >> 1) & 1), a.err, a.wait_us));
       if (!ok) {
-        if (tid == 0 && tn < ntiles)
-          mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+        if (tid == 0 && tn < ntiles && !a.test_skip_copy)
+          mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr, a.wait_us);
         abort = true;
         break;
       }

@@ -13,15 +13,21 @@
 // Costs of that choice, which callers must accept:
 //  * every GPU that loads the library holds the arrays (about 2.2 MB) until
 //    the process exits, used or not;
-//  * every call on a device shares them: calls whose work overlaps on that
-//    GPU (different streams, host threads or processes' graphs) race and
-//    corrupt each other's results; serialise them (one stream, or events);
+//  * every call on a device, from any stream or host thread of this process,
+//    shares them: calls whose work overlaps on that GPU race and corrupt each
+//    other's results; serialise them (one stream, or events). (Each process
+//    has its own copy of the arrays in its own CUDA context.);
 //  * the first call on each device looks the arrays' device addresses up
-//    with cudaGetSymbolAddress (which may load the module); make that first
-//    call before any stream capture.
+//    with cudaGetSymbolAddress (which may load the module) and keeps them for
+//    the life of the process: cudaDeviceReset between calls is not supported
+//    (the kept addresses would be stale);
+//  * every call copies its host-made tables with cudaMemcpyAsync from host
+//    stack arrays and ends with cudaStreamSynchronize, so no call can be made
+//    while its stream is being captured into a CUDA graph.
 // The host side computes the FP64 cosmology and tables with ordinary host
-// code (as gg_plan does); nothing here allocates device memory or calls an
-// allocating CUDA or PyTorch routine.
+// code (as gg_plan does), evaluating the cosmology model once per call;
+// nothing here allocates device memory or calls an allocating CUDA or
+// PyTorch routine.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -85,14 +91,11 @@ gg_status scratch_for_current_device(Scratch **out) {
 }
 
 template <typename R>
-gg_status run(const gg_params *p, uint64_t seed, const void *noise, void *delta, cudaStream_t st,
-              const Scratch &s) {
+gg_status run(const gg_params *p, const gg_info &info, const double *sd, uint64_t seed,
+              const void *noise, void *delta, cudaStream_t st, const Scratch &s) {
   const int n = (int)p->n, half = n / 2;
-  gg_info info{};
-  if (gg_cosmo_eval(p, &info) != GG_OK) return GG_EINVAL;  // message already set
   // tables in FP64 on the host, rounded once, copied into the scratch arrays
   R tw_n[2 * kMaxN], tw_half[2 * kMaxHalf], tab[kMaxTable];
-  double sd[kMaxTable];
   for (int i = 0; i < n; ++i) {
     tw_n[2 * i] = (R)std::cos(-2.0 * kPi * i / n);
     tw_n[2 * i + 1] = (R)std::sin(-2.0 * kPi * i / n);
@@ -102,7 +105,6 @@ gg_status run(const gg_params *p, uint64_t seed, const void *noise, void *delta,
     tw_half[2 * i + 1] = (R)std::sin(-2.0 * kPi * i / half);
   }
   const int count = 3 * half * half + 1;
-  if (gg_filter_table(p, sd, count) != GG_OK) return GG_EINVAL;
   const double norm = 1.0 / std::pow((double)n, 1.5);
   for (int i = 0; i < count; ++i) tab[i] = (R)(sd[i] * norm);
   cudaError_t e;
@@ -127,8 +129,7 @@ gg_status run(const gg_params *p, uint64_t seed, const void *noise, void *delta,
   z.st = st_half;
   z.tw_half = s.tw_half;
   z.tw_full = s.tw_n;
-  int lines = 1;
-  while (lines * 2 * (half / st_half.e) <= 256 && lines < 64) lines *= 2;
+  const int lines = gg::z_lines_per_cta<R>(st_half);  // the rule gg_plan uses
   z.lines_per_cta = lines;
   e = spec ? gg::spec_zfwd<R>(z, st) : gg::launch_zfwd<R>(z, st);
   if (e != cudaSuccess) return fail(GG_ECUDA, cudaGetErrorString(e));
@@ -181,7 +182,7 @@ gg_status run(const gg_params *p, uint64_t seed, const void *noise, void *delta,
   if ((e = cudaMemcpyAsync(&word, s.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)  // also keeps the host tables alive until used
     return fail(GG_ECUDA, cudaGetErrorString(e));
-  if (word) return fail(word == 2 ? GG_ETIMEOUT : GG_EDEVICE, "device reported an error");
+  if (word) return fail(word == 2 ? GG_ETIMEOUT : GG_ECUDA, "device reported an error");
   return GG_OK;
 }
 
@@ -190,8 +191,6 @@ gg_status run(const gg_params *p, uint64_t seed, const void *noise, void *delta,
 extern "C" gg_status gg_gaussian_field_static(const gg_params *p, uint64_t seed,
                                               const void *noise_dev, void *delta_dev, void *stream) {
   if (!p) return fail(GG_EINVAL, "gg_gaussian_field_static: params is NULL");
-  gg_info probe{};
-  if (gg_cosmo_eval(p, &probe) != GG_OK) return GG_EINVAL;  // invalid parameters, message set
   if (p->n > kMaxN) {
     char msg[200];
     std::snprintf(msg, sizeof msg,
@@ -200,11 +199,20 @@ extern "C" gg_status gg_gaussian_field_static(const gg_params *p, uint64_t seed,
                   (long long)p->n, kMaxN);
     return fail(GG_EINVAL, msg);
   }
+  // the cosmology and the Eq. 1 filter from one evaluation of the model
+  // (also the parameter check: invalid parameters as in gg_plan)
+  gg_info info{};
+  double sd[kMaxTable];
+  const int half = p->n > 0 ? (int)(p->n / 2) : 0;
+  const char *why = nullptr;
+  if (!gg::info_and_filter(p, &info, sd, 3 * (int64_t)half * half + 1, &why))
+    return fail(GG_EINVAL, why ? why : "invalid parameters");
   if (!delta_dev || ((uintptr_t)delta_dev & 15u) || ((uintptr_t)noise_dev & 15u))
     return fail(GG_EINVAL, "gg_gaussian_field_static: delta_dev NULL or a buffer unaligned");
   Scratch *s = nullptr;
   gg_status stt = scratch_for_current_device(&s);
   if (stt != GG_OK) return stt;
-  return p->prec == GG_F64 ? run<double>(p, seed, noise_dev, delta_dev, (cudaStream_t)stream, *s)
-                           : run<float>(p, seed, noise_dev, delta_dev, (cudaStream_t)stream, *s);
+  const cudaStream_t st = (cudaStream_t)stream;
+  return p->prec == GG_F64 ? run<double>(p, info, sd, seed, noise_dev, delta_dev, st, *s)
+                           : run<float>(p, info, sd, seed, noise_dev, delta_dev, st, *s);
 }

@@ -13,7 +13,13 @@ this size, so:
 * Eq. 4's top hat at this size: the planted mode comes out unchanged above
   the cut and vanishes below it;
 * the pos + vel-only path agrees bit for bit with the path that also writes
-  psi.
+  psi;
+* a random field of 64 planted Fourier modes (random amplitudes and phases,
+  modes with |m_j| = N/2 - 1, modes at multiples of 3, modes with all three
+  m_j != 0) gives, at 10^5 sampled cells, the closed-form sum of the modes'
+  displacements built from the oracle's P(k) and growth, for psi, pos and vel
+  of the FP32 path (1e-5) and psi of the FP64 path (1e-11): an
+  oracle-anchored check of both 1536 codelets on a field with many modes.
 """
 import math
 
@@ -193,5 +199,111 @@ def test_pos_vel_only_bit_identical(gg):
         plan.sync()
         assert torch.equal(pos, pos2) and torch.equal(vel, vel2), j
     del pos, vel, pos2, vel2, psi
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def _modes(seed=5, count=64):
+    """Random distinct modes m (|m_j| <= N/2 - 1, m != 0), amplitudes, phases."""
+    rng = np.random.default_rng(seed)
+    h = N // 2 - 1
+    out = set()
+    while len(out) < count:
+        t = len(out)
+        m = rng.integers(-h, h + 1, size=3)
+        if t < 12:  # an edge of the kept band on one axis
+            m[t % 3] = h if t % 2 else -h
+        elif t < 24:  # multiples of 3 on every axis (radix-3 stage inputs)
+            m = 3 * rng.integers(-(h // 3), h // 3 + 1, size=3)
+        elif t < 40:  # low |m|: the largest displacements
+            m = rng.integers(-8, 9, size=3)
+        if (m != 0).all() or (t < 12 and m.any()):
+            out.add(tuple(int(v) for v in m))
+    modes = np.array(sorted(out), dtype=np.int64)
+    return modes, rng.uniform(0.5, 2.0, size=count), rng.uniform(0.0, 2 * math.pi, size=count)
+
+
+def _mode_noise(modes, amp, ph, dtype):
+    """W(x_n) = sum_t a_t cos(2 pi m_t.n / N + phi_t) on the device, in FP64
+    (phases reduced exactly in integers), stored in `dtype`."""
+    noise = torch.empty((N, N, N), dtype=dtype, device="cuda")
+    i = torch.arange(N, device="cuda", dtype=torch.int64)
+    for x0 in range(0, N, 64):
+        acc = torch.zeros((64, N, N), dtype=torch.float64, device="cuda")
+        for (mx, my, mz), a, p in zip(modes.tolist(), amp.tolist(), ph.tolist()):
+            r = (mx * i[x0:x0 + 64, None, None] + my * i[None, :, None] + mz * i[None, None, :]) % N
+            acc += a * torch.cos(r.double() * (2 * math.pi / N) + p)
+            del r
+        noise[x0:x0 + 64] = acc.to(dtype)
+        del acc
+    return noise
+
+
+def _mode_psi(modes, amp, ph, idx, c, growth):
+    """Closed form at cells idx: psi_j = -sum_t a_t s_t k_j/|k|^2 sin(k.x + phi_t),
+    s_t = D sqrt(P(|k_t|) N^3 / V) (Eqs. 1-2 for one planted mode, summed)."""
+    ix, iy, iz = idx // (N * N), (idx // N) % N, idx % N
+    psi = np.zeros((3, idx.size))
+    for (mx, my, mz), a, p in zip(modes.tolist(), amp.tolist(), ph.tolist()):
+        k = 2 * math.pi / BOX * np.array([mx, my, mz], dtype=float)
+        kk = math.sqrt((k ** 2).sum())
+        s = growth * math.sqrt(float(c.power(kk)) * N ** 3 / BOX ** 3)
+        r = (mx * ix + my * iy + mz * iz) % N
+        sn = np.sin(2 * math.pi * r / N + p)
+        for j in range(3):
+            psi[j] -= a * s * k[j] / kk ** 2 * sn
+    return psi
+
+
+def test_multimode_field_closed_form_fp32(gg):
+    from tests.oracle_cases import cosmology_from
+    c = cosmology_from(EH_NW)
+    a_init = 1.0 / (1.0 + Z)
+    modes, amp, ph = _modes()
+    noise = _mode_noise(modes, amp, ph, torch.float32)
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f32")
+    e = lambda: torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    out = {"psi": [e() for _ in range(3)], "pos": [e() for _ in range(3)],
+           "vel": [e() for _ in range(3)]}
+    plan.zeldovich(noise=noise, out=out)
+    plan.sync()
+    del noise
+    idx = _sample_idx(100000, 3)
+    want = _mode_psi(modes, amp, ph, idx, c, c.growth(a_init))
+    vfac = c.velocity_factor(a_init)
+    it = torch.from_numpy(idx).cuda()
+    ulp = np.spacing(np.float32(BOX))
+    for j in range(3):
+        got = {k: out[k][j].reshape(-1)[it].cpu().numpy().astype(np.float64)
+               for k in ("psi", "pos", "vel")}
+        rel = lambda x, y: np.linalg.norm(x - y) / np.linalg.norm(y)
+        assert rel(got["psi"], want[j]) < 1e-5, j
+        assert rel(got["vel"], vfac * want[j]) < 1e-5, j
+        q = (np.array([idx // (N * N), (idx // N) % N, idx % N])[j] + 0.5) * (BOX / N)
+        d = got["pos"] - (q + want[j])
+        d -= BOX * np.round(d / BOX)
+        assert np.abs(d).max() < 4 * ulp + 1e-5 * np.abs(want[j]).max(), j
+    del out
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def test_multimode_field_closed_form_fp64(gg):
+    from tests.oracle_cases import cosmology_from
+    c = cosmology_from(EH_NW)
+    modes, amp, ph = _modes()
+    noise = _mode_noise(modes, amp, ph, torch.float64)
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f64")
+    psi = torch.empty((N, N, N), dtype=torch.float64, device="cuda")
+    idx = _sample_idx(100000, 4)
+    want = _mode_psi(modes, amp, ph, idx, c, c.growth(1.0 / (1.0 + Z)))
+    it = torch.from_numpy(idx).cuda()
+    for j in range(3):
+        plan.zeldovich(noise=noise, out={"psi": [psi if a == j else None for a in range(3)],
+                                         "pos": [None] * 3, "vel": [None] * 3})
+        plan.sync()
+        got = psi.reshape(-1)[it].cpu().numpy()
+        assert np.linalg.norm(got - want[j]) / np.linalg.norm(want[j]) < 1e-11, j
+    del noise, psi
     plan.close()
     torch.cuda.empty_cache()

@@ -104,6 +104,27 @@ def test_zeldovich_fp32_matches_oracle(gg, n):
     _compare(out, run_oracle(w, seed=3), w["box"], "f32")
 
 
+@pytest.mark.parametrize("n,prec", [(256, "f32"), (384, "f32"), (384, "f64")])
+def test_batched_workload_sizes_match_oracle(gg, n, prec):
+    """The size-specialised codelets of the batched workload's larger grids
+    (N = 256: radix 8.8.4; N = 384: 8.8.2.3 with 24 elements a thread and
+    register stage pairs) against the oracle on Philox noise, with that
+    workload's cell size (L = N Mpc/h) and z = 50, in the autotuner's
+    variants and in variant 0."""
+    w = dict(n=n, box=float(n), cosmo=BBKS, z_init=50.0)
+    ora = run_oracle(w, seed=5)
+    plan = gg.Plan(n, w["box"], BBKS, 50.0, prec)
+    for tune in (False, True):
+        if tune:
+            plan.autotune(1)
+        out = plan.zeldovich(seed=5)
+        plan.sync()
+        _compare(out, ora, w["box"], prec)
+        del out
+    plan.close()
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_caller_noise_and_eh(gg, prec):
     n = 32

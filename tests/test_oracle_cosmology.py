@@ -118,3 +118,98 @@ def test_table_transfer_reproduces_analytic():
     tab = Cosmology(0.3, 0.7, 0.96, 0.8, tf="table", tab_k=tk, tab_p=a.power(tk) * 3.0)
     k = np.array([0.01, 0.1, 1.0])
     np.testing.assert_allclose(tab.power(k), a.power(k), rtol=2e-4)
+
+
+# ---------------------------------------------------------------------------
+# Transfer-function coefficients, pinned by the series and asymptotes that the
+# published formulas fix (derived by hand from BBKS eq. G3 and EH98 eq. 29,
+# not by evaluating the formulas again):
+#   BBKS, q -> 0:   T = 1 - (2.34/2 + 3.89/4) q
+#                         + (2.34^2/3 + (2.34/2)(3.89/4) - 16.1^2/4 + (5/32) 3.89^2) q^2 + O(q^3)
+#   BBKS, q -> oo:  T (2.34 q)(6.71 q) / ln(1 + 2.34 q) = 1 - 5.46^3 / (4 6.71^4 q) + O(q^-2)
+#   EH98, q -> 0:   (1 - T0) / q^2 -> (14.2 + 731) / ln(2e)
+#   EH98, q -> oo:  T0 q^2 14.2 / ln(2e + 1.8 q) = 1 - (731/62.5)/(14.2 q) + O(q^-2)
+# A mistyped coefficient moves one of these limits.
+
+def test_bbks_series_at_small_q():
+    t = Cosmology.bbks_of_q
+    c1 = 2.34 / 2 + 3.89 / 4
+    c2 = 2.34 ** 2 / 3 + (2.34 / 2) * (3.89 / 4) - 16.1 ** 2 / 4 + (5 / 32) * 3.89 ** 2
+    for q in (1e-6, 2e-6):  # the q^3 term (coefficient about 340) bounds the difference
+        assert abs((1 - float(t(q))) / q - (c1 - c2 * q)) < 500 * q * q
+    # second coefficient by Richardson extrapolation (removes the q^3 term)
+    r = lambda q: (float(t(q)) - 1 + c1 * q) / q ** 2
+    assert abs(2 * r(5e-6) - r(1e-5) - c2) < 1e-5 * abs(c2)
+
+
+def test_bbks_asymptote_at_large_q():
+    t = Cosmology.bbks_of_q
+    d1 = -5.46 ** 3 / (4 * 6.71 ** 4)
+    for q in (1e5, 1e6):
+        g = float(t(q)) * (2.34 * q) * (6.71 * q) / math.log1p(2.34 * q)
+        assert abs((g - 1) * q - d1) < 2e-5 * abs(d1) * (1e6 / q)
+
+
+def test_eh_shape_series_at_small_q():
+    t = Cosmology.eh_t0_of_q
+    r = lambda q: (1 - float(t(q))) / q ** 2
+    # r is linear in q near 0 (731/(1 + 62.5 q) and ln(2e + 1.8 q)): Richardson
+    lim = 2 * r(5e-6) - r(1e-5)
+    assert abs(lim - (14.2 + 731.0) / math.log(2 * math.e)) < 1e-6 * lim
+
+
+def test_eh_shape_asymptote_at_large_q():
+    t = Cosmology.eh_t0_of_q
+    d1 = -(731.0 / 62.5) / 14.2
+    for q in (1e6, 1e8):
+        g = float(t(q)) * q * q * 14.2 / math.log(2 * math.e + 1.8 * q)
+        assert abs((g - 1) * q - d1) < 1e-4 * abs(d1)
+
+
+def test_eh_gamma_eff_limits():
+    c = cosmology_from(EH_NW)
+    gam = c.eh_gamma_eff(np.array([1e-8, 1e6]))
+    fb = c.omega_b / c.omega_m
+    assert abs(gam[0] / (c.omega_m * c.h) - 1) < 1e-12
+    assert 0.5 < gam[1] / (c.omega_m * c.h) < 1.0  # alpha < 1 with baryons
+    nob = Cosmology(0.31, 0.68, 0.965, 0.81, tf="eh_nw", omega_b=1e-12)
+    g2 = nob.eh_gamma_eff(np.array([1e-8, 1e6]))
+    assert np.allclose(g2, 0.31 * 0.68, rtol=1e-9) and fb > 0
+
+
+@pytest.mark.parametrize("cfg", [BBKS, EH_NW])
+def test_sigma8_certified_by_gauss_legendre(cfg):
+    """sigma(8) of the normalised P(k) by composite 16-point Gauss-Legendre:
+    4000 pieces in ln k below k = 1/R, then pieces of pi/(4R) in k up to
+    1e3 h/Mpc (a quarter of the window's oscillation each), all vectorised:
+    an integration entirely unlike the oracle's adaptive quadrature."""
+    from scipy.special import roots_legendre
+    c = cosmology_from(cfg)
+    radius = 8.0
+    x, w = roots_legendre(16)
+
+    def gl(edges, f):
+        lo, hi = edges[:-1, None], edges[1:, None]
+        pts = 0.5 * (lo + hi) + 0.5 * (hi - lo) * x[None, :]
+        return float(np.sum(0.5 * (hi - lo) * w[None, :] * f(pts)))
+
+    def win2(xx):
+        full = 3 * (np.sin(xx) - xx * np.cos(xx)) / np.where(xx < 1e-2, 1.0, xx) ** 3
+        return np.where(xx < 1e-2, 1 - xx * xx / 10 + xx ** 4 / 280, full) ** 2
+
+    kb = 1.0 / radius
+    e1 = np.linspace(math.log(1e-6), math.log(kb), 4001)
+    i1 = gl(e1, lambda l: np.exp(3 * l) * c.power(np.exp(l)) * win2(np.exp(l) * radius))
+    e2 = np.append(np.arange(kb, 1e3, math.pi / (4 * radius)), 1e3)
+    i2 = gl(e2, lambda k: k * k * c.power(k) * win2(k * radius))
+    sigma = math.sqrt((i1 + i2) / (2 * math.pi ** 2))
+    assert abs(sigma / c.sigma_8 - 1) < 1e-12
+
+
+def test_variance_integration_has_no_quadrature_warnings():
+    import warnings
+    for cfg in (BBKS, EH_NW):
+        c = cosmology_from(cfg)
+        with warnings.catch_warnings():
+            warnings.simplefilter("error")
+            c.amplitude()
