@@ -17,6 +17,19 @@ namespace gg {
 namespace ct {
 
 // ------------------------------------------------------------ schedules
+// A schedule is named by a key: the transform length n, plus kBig for the
+// FP32 codelets. Those take a few large radices where a thread can hold a
+// whole butterfly (n = 256: 16 x 16; n = 512: 32 x 16): each radix is one
+// DFT in registers (constant twiddles inside it), so a transform makes one
+// shared-memory round trip and one twiddle stage instead of two or three of
+// each. Other lengths, and every FP64 codelet (whose bound is the FP64
+// pipe, not the stage count), use radix 8 first, then 4 or 2, then the 3s.
+constexpr int kBig = 1 << 20;
+template <typename R> __host__ __device__ constexpr int skey(int n) {
+  return sizeof(R) == 4 ? (n | kBig) : n;
+}
+__host__ __device__ constexpr int key_n(int key) { return key & (kBig - 1); }
+
 struct Fac {
   int a, b;  // n = 2^a 3^b
 };
@@ -26,13 +39,30 @@ __host__ __device__ constexpr Fac factor(int n) {
   while (n % 3 == 0) { n /= 3; ++f.b; }
   return f;
 }
-__host__ __device__ constexpr int nstages(int n) {
-  const Fac f = factor(n);
+// large-radix forward schedules of the FP32 codelets (0: none at this n / stage)
+__host__ __device__ constexpr int big_radix(int n, int s) {
+  switch (n) {
+    case 256: return s < 2 ? 16 : 0;
+    case 512: return s == 0 ? 32 : (s == 1 ? 16 : 0);
+    default: return 0;
+  }
+}
+__host__ __device__ constexpr bool is_big(int key) {
+  return (key & kBig) != 0 && big_radix(key_n(key), 0) != 0;
+}
+__host__ __device__ constexpr int nstages(int key) {
+  if (is_big(key)) {
+    int c = 0;
+    while (big_radix(key_n(key), c)) ++c;
+    return c;
+  }
+  const Fac f = factor(key_n(key));
   return f.a / 3 + (f.a % 3 ? 1 : 0) + f.b;
 }
-// forward schedule: radix 8 first, then 4 or 2, then the 3s
-__host__ __device__ constexpr int radix_fwd(int n, int s) {
-  const Fac f = factor(n);
+// forward schedule: radix 8 first, then 4 or 2, then the 3s (or the large radices)
+__host__ __device__ constexpr int radix_fwd(int key, int s) {
+  if (is_big(key)) return big_radix(key_n(key), s);
+  const Fac f = factor(key_n(key));
   const int n8 = f.a / 3;
   if (s < n8) return 8;
   s -= n8;
@@ -44,20 +74,139 @@ __host__ __device__ constexpr int radix_fwd(int n, int s) {
 }
 // the inverse transforms use the same radices in reverse order, so that the
 // first inverse stage has the radix of the last forward stage
-__host__ __device__ constexpr int radix_of(int n, int s, bool inv) {
-  return inv ? radix_fwd(n, nstages(n) - 1 - s) : radix_fwd(n, s);
+__host__ __device__ constexpr int radix_of(int key, int s, bool inv) {
+  return inv ? radix_fwd(key, nstages(key) - 1 - s) : radix_fwd(key, s);
 }
-__host__ __device__ constexpr int ns_of(int n, int s, bool inv) {
+__host__ __device__ constexpr int ns_of(int key, int s, bool inv) {
   int p = 1;
-  for (int i = 0; i < s; ++i) p *= radix_of(n, i, inv);
+  for (int i = 0; i < s; ++i) p *= radix_of(key, i, inv);
   return p;
 }
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b ? gcd_c(b, a % b) : a; }
 // elements per thread: the least common multiple of the radices
-__host__ __device__ constexpr int elems(int n) {
-  const Fac f = factor(n);
-  const int p2 = f.a >= 3 ? 8 : (f.a == 2 ? 4 : (f.a == 1 ? 2 : 1));
-  return p2 * (f.b ? 3 : 1);
+__host__ __device__ constexpr int elems(int key) {
+  int e = 1;
+  for (int s = 0; s < nstages(key); ++s) {
+    const int r = radix_fwd(key, s);
+    e = e / gcd_c(e, r) * r;
+  }
+  return e;
 }
+
+// ------------------------------------------------ in-register DFTs of composite length
+// cos and sin of 2 pi m / r in FP64 at compile time: exact reduction to a
+// quadrant, then the Taylor series on [0, pi/2) (terms to x^29: error below
+// 1e-20), then the quadrant's exact rotation.
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 15; ++i) {
+    t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    s += t;
+  }
+  return s;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 15; ++i) {
+    t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    s += t;
+  }
+  return s;
+}
+__host__ __device__ constexpr double cos_turn(int m, int r) {
+  m = ((m % r) + r) % r;
+  const int q = 4 * m / r, rem = 4 * m - q * r;  // angle = (q + rem / r) pi / 2
+  const double x = 1.57079632679489661923132169163975 * (double)rem / (double)r;
+  const double c = taylor_cos(x), s = taylor_sin(x);
+  return q == 0 ? c : (q == 1 ? -s : (q == 2 ? -c : s));
+}
+__host__ __device__ constexpr double sin_turn(int m, int r) {
+  m = ((m % r) + r) % r;
+  const int q = 4 * m / r, rem = 4 * m - q * r;
+  const double x = 1.57079632679489661923132169163975 * (double)rem / (double)r;
+  const double c = taylor_cos(x), s = taylor_sin(x);
+  return q == 0 ? s : (q == 1 ? c : (q == 2 ? -s : -c));
+}
+
+template <int I, int END, class F> __device__ __forceinline__ void static_for(const F &f) {
+  if constexpr (I < END) {
+    f(IntC<I>{});
+    static_for<I + 1, END>(f);
+  }
+}
+
+// a * w^E with w = exp(-2 pi i / RT) (forward) or its conjugate (INV), E a
+// compile-time exponent: no arithmetic for w^E = 1, a swap for +-i, a sign
+// for -1, two adds and two multiplies for the odd eighths, else a complex
+// product with the FP64-computed constant rounded once.
+template <int RT, int EXP, bool INV, typename T> __device__ __forceinline__ T tw_const(T a) {
+  using R = decltype(a.x);
+  constexpr int e = ((EXP % RT) + RT) % RT;
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (2 * e == RT) {
+    return T{-a.x, -a.y};
+  } else if constexpr (4 * e == RT) {
+    return mul_wi<INV>(a);  // -i forward
+  } else if constexpr (4 * e == 3 * RT) {
+    return mul_wi<!INV>(a);  // +i forward
+  } else if constexpr ((8 * e) % RT == 0) {  // (+-1 +- i) / sqrt 2
+    constexpr R h = (R)0.70710678118654752440;
+    constexpr int o = 8 * e / RT;  // 1, 3, 5, 7
+    constexpr R c = (o == 1 || o == 7) ? h : -h;
+    constexpr R sn = (o == 1 || o == 3) ? -h : h;  // imaginary part of w^e (forward)
+    constexpr R si = INV ? -sn : sn;
+    // a * (c + i si) with |c| = |si| = h: h * (+-a.x -+ a.y, ...)
+    if constexpr (c > 0 && si < 0) return T{h * (a.x + a.y), h * (a.y - a.x)};
+    else if constexpr (c > 0 && si > 0) return T{h * (a.x - a.y), h * (a.y + a.x)};
+    else if constexpr (c < 0 && si < 0) return T{-h * (a.x - a.y), -h * (a.y + a.x)};
+    else return T{-h * (a.x + a.y), h * (a.x - a.y)};
+  } else {
+    constexpr R c = (R)cos_turn(e, RT);
+    constexpr R sn = (R)(INV ? sin_turn(e, RT) : -sin_turn(e, RT));
+    return T{a.x * c - a.y * sn, a.x * sn + a.y * c};
+  }
+}
+
+}  // namespace ct
+
+// DFT of length R1 * R2 on registers in natural order (input n, output k):
+// n = R2 n1 + n2, k = k1 + R1 k2; a length-R1 DFT over n1 for each n2, the
+// twiddle w_R^(n2 k1), then a length-R2 DFT over n2 for each k1.
+template <int R1, int R2, bool INV, typename T> struct ComposedDft {
+  static __device__ __forceinline__ void run(T *v) {
+    constexpr int RT = R1 * R2;
+    T t[RT];
+    ct::static_for<0, R2>([&](auto n2c) {
+      constexpr int n2 = decltype(n2c)::value;
+      T u[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) u[n1] = v[R2 * n1 + n2];
+      Butterfly<R1, INV, T>::run(u);
+      ct::static_for<0, R1>([&](auto k1c) {
+        constexpr int k1 = decltype(k1c)::value;
+        t[n2 * R1 + k1] = ct::tw_const<RT, n2 * k1, INV>(u[k1]);
+      });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      T u[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) u[n2] = t[n2 * R1 + k1];
+      Butterfly<R2, INV, T>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = u[k2];
+    }
+  }
+};
+template <bool INV, typename T> struct Butterfly<6, INV, T> : ComposedDft<2, 3, INV, T> {};
+template <bool INV, typename T> struct Butterfly<12, INV, T> : ComposedDft<4, 3, INV, T> {};
+template <bool INV, typename T> struct Butterfly<16, INV, T> : ComposedDft<4, 4, INV, T> {};
+template <bool INV, typename T> struct Butterfly<24, INV, T> : ComposedDft<8, 3, INV, T> {};
+template <bool INV, typename T> struct Butterfly<32, INV, T> : ComposedDft<8, 4, INV, T> {};
+template <bool INV, typename T> struct Butterfly<48, INV, T> : ComposedDft<16, 3, INV, T> {};
+
+namespace ct {
 
 // k = j mod NS for j = p + P*b, 0 <= p < P, 0 <= b < NB, folded at compile time
 template <int NS, int P, int NB>
@@ -70,6 +219,28 @@ __device__ __forceinline__ int k_of(int p, int b) {
     return p + P * b;  // j < NS
   } else {
     return (p + P * b) % NS;
+  }
+}
+
+// Twiddles of a stage with NS > 1: FP32 radices up to 8 load w^1 per
+// butterfly (before the stage's shared-memory reads, to overlap their
+// latency) and form the other powers by at most three products; FP64, and
+// the large FP32 radices, read every power w^(k r) from the table (an FP32
+// power chain over 15 or 31 steps would lose accuracy).
+template <typename R, int RAD> __host__ __device__ constexpr bool powers_from_w1() {
+  return sizeof(R) == 4 && (RAD == 2 || RAD == 3 || RAD == 4 || RAD == 8);
+}
+template <typename R, int RAD, bool INV, int TSTEP>
+__device__ __forceinline__ void stage_twiddles(Cx<R> *v, int k, Cx<R> w1,
+                                               const Cx<R> *__restrict__ tw) {
+  if constexpr (powers_from_w1<R, RAD>()) {
+    twiddle_powers<RAD, INV>(v, w1);
+  } else {
+#pragma unroll
+    for (int r = 1; r < RAD; ++r) {
+      const Cx<R> w = ldg_c(tw + k * TSTEP * r);
+      v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
   }
 }
 
@@ -88,12 +259,13 @@ template <int SY> __device__ __forceinline__ void stage_barrier() {
 template <typename R, int N, int E, int SI, bool INV, int SY, class Ld, class St>
 __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                       const St &st) {
-  constexpr int RAD = radix_of(N, SI, INV);
-  constexpr int NS = ns_of(N, SI, INV);
+  constexpr int K = skey<R>(N);
+  constexpr int RAD = radix_of(K, SI, INV);
+  constexpr int NS = ns_of(K, SI, INV);
   constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
   asm volatile("" : "+r"(p));
   Cx<R> w1[NB];
-  if constexpr (NS > 1 && sizeof(R) == 4) {
+  if constexpr (NS > 1 && powers_from_w1<R, RAD>()) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) w1[b] = ldg_c(tw + k_of<NS, P, NB>(p, b) * TSTEP);
   }
@@ -105,18 +277,8 @@ __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const
   stage_barrier<SY>();
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
-    if constexpr (NS > 1) {
-      if constexpr (sizeof(R) == 4) {
-        twiddle_powers<RAD, INV>(&v[b * RAD], w1[b]);
-      } else {
-        const int k = k_of<NS, P, NB>(p, b);
-#pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-          const Cx<R> w = ldg_c(tw + k * TSTEP * r);
-          v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
-        }
-      }
-    }
+    if constexpr (NS > 1)
+      stage_twiddles<R, RAD, INV, TSTEP>(&v[b * RAD], k_of<NS, P, NB>(p, b), w1[b], tw);
     Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
   }
 #pragma unroll
@@ -159,14 +321,15 @@ __device__ __forceinline__ void stages_pingpong(int p, const Cx<R> *__restrict__
 template <typename R, int N, int E, bool INV, class Ld>
 __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
                                                 Cx<R> *v) {
-  constexpr int S = nstages(N);
-  constexpr int RAD = radix_of(N, S - 1, INV);
-  constexpr int NS = ns_of(N, S - 1, INV);
+  constexpr int K = skey<R>(N);
+  constexpr int S = nstages(K);
+  constexpr int RAD = radix_of(K, S - 1, INV);
+  constexpr int NS = ns_of(K, S - 1, INV);
   constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
   static_assert(NS * RAD == N, "last stage");
   asm volatile("" : "+r"(p));
   Cx<R> w1[NB];
-  if constexpr (NS > 1 && sizeof(R) == 4) {
+  if constexpr (NS > 1 && powers_from_w1<R, RAD>()) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) w1[b] = ldg_c(tw + k_of<NS, P, NB>(p, b) * TSTEP);
   }
@@ -176,18 +339,8 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
     for (int r = 0; r < RAD; ++r) v[b * RAD + r] = ld(p + P * b + r * SPAN);
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
-    if constexpr (NS > 1) {
-      if constexpr (sizeof(R) == 4) {
-        twiddle_powers<RAD, INV>(&v[b * RAD], w1[b]);
-      } else {
-        const int k = k_of<NS, P, NB>(p, b);
-#pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-          const Cx<R> w = ldg_c(tw + k * TSTEP * r);
-          v[b * RAD + r] = INV ? cmulc(v[b * RAD + r], w) : cmul(v[b * RAD + r], w);
-        }
-      }
-    }
+    if constexpr (NS > 1)
+      stage_twiddles<R, RAD, INV, TSTEP>(&v[b * RAD], k_of<NS, P, NB>(p, b), w1[b], tw);
     Butterfly<RAD, INV, Cx<R>>::run(&v[b * RAD]);
   }
 }
@@ -199,8 +352,9 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
 // so the pair runs in registers without a shared-memory round trip between
 // them. Same twiddles, butterflies and order of operations as the two
 // separate stages.
-template <int N, int E> __host__ __device__ constexpr bool fuse_pair() {
-  return nstages(N) >= 3 && E % (radix_fwd(N, nstages(N) - 2) * radix_fwd(N, nstages(N) - 1)) == 0;
+template <typename R, int N, int E> __host__ __device__ constexpr bool fuse_pair() {
+  constexpr int K = skey<R>(N);
+  return nstages(K) >= 3 && E % (radix_fwd(K, nstages(K) - 2) * radix_fwd(K, nstages(K) - 1)) == 0;
 }
 
 // Twiddles w^(k r), r = 1 .. RAD-1, on one butterfly's inputs; kt = k*TSTEP.
@@ -224,9 +378,10 @@ __device__ __forceinline__ void stage_twiddle(Cx<R> *v, const Cx<R> *__restrict_
 template <typename R, int N, int E, class Ld>
 __device__ __forceinline__ void last_two_stages_regs(int p, const Cx<R> *__restrict__ tw,
                                                      const Ld &ld, Cx<R> *v) {
-  constexpr int S = nstages(N);
-  constexpr int RA = radix_of(N, S - 2, false), RB = radix_of(N, S - 1, false);
-  constexpr int NSA = ns_of(N, S - 2, false);
+  constexpr int K = skey<R>(N);
+  constexpr int S = nstages(K);
+  constexpr int RA = radix_of(K, S - 2, false), RB = radix_of(K, S - 1, false);
+  constexpr int NSA = ns_of(K, S - 2, false);
   constexpr int P = N / E, G = E / (RA * RB), NBA = E / RA, NBB = E / RB;
   constexpr int SPANA = N / RA, TSA = N / (NSA * RA);
   static_assert(NSA == P * G && NSA * RA * RB == N, "register pair");
@@ -271,7 +426,7 @@ __device__ __forceinline__ void last_two_stages_regs(int p, const Cx<R> *__restr
 // (g, r); inverse_head_store writes them.
 template <typename R, int N, int E>
 __device__ __forceinline__ void inverse_head_regs(const Cx<R> *__restrict__ tw, Cx<R> *v) {
-  constexpr int RA = radix_of(N, 0, true), RB = radix_of(N, 1, true);
+  constexpr int RA = radix_of(skey<R>(N), 0, true), RB = radix_of(skey<R>(N), 1, true);
   constexpr int P = N / E, G = E / (RA * RB), NBA = E / RA;
   constexpr int TSB = N / (RA * RB);
 #pragma unroll
@@ -297,7 +452,7 @@ __device__ __forceinline__ void inverse_head_regs(const Cx<R> *__restrict__ tw, 
 // Stage B's outputs: element s of butterfly j' goes to (j' - k)*RB + k + s*RA.
 template <typename R, int N, int E, class St>
 __device__ __forceinline__ void inverse_head_store(int p, const Cx<R> *v, const St &st) {
-  constexpr int RA = radix_of(N, 0, true), RB = radix_of(N, 1, true);
+  constexpr int RA = radix_of(skey<R>(N), 0, true), RB = radix_of(skey<R>(N), 1, true);
   constexpr int P = N / E, G = E / (RA * RB);
 #pragma unroll
   for (int g = 0; g < G; ++g)
@@ -323,27 +478,40 @@ __device__ __forceinline__ void inverse_head_store(int p, const Cx<R> *v, const 
 // in shared memory and every output reads it from there.
 template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int CB = 2 * (int)sizeof(R);
-  static constexpr int E0 = elems(N);
+  static constexpr bool BIG = is_big(skey<R>(N));
+  static constexpr int E0 = elems(skey<R>(N));
   static constexpr bool DOUBLE_OK = N % (2 * E0) == 0 && 2 * E0 * ((int)sizeof(R) / 4) <= 16;
   static constexpr int E = (V >= 1 && DOUBLE_OK) ? 2 * E0 : E0;
   static constexpr int P = N / E;
+  // large-radix schedules (E cannot double): variant 1 is the small tile of
+  // variant 2 with the handed-off spectrum parked in shared memory, so that
+  // three CTAs' registers fit an SM
+  static constexpr bool SMALL = V == 2 || (BIG && V == 1);
   static constexpr int pick() {
     int b = 128 / CB;
     while (b > 1 && ((N / 2) % b != 0 || P * b > 512 || 2 * (N * b * CB) > 200 * 1024)) b /= 2;
-    if (V == 2 && b * CB > 32) b /= 2;
+    if (SMALL && b * CB > 32) b /= 2;
     return b;
   }
   static constexpr int B = pick();
   static constexpr int THREADS = P * B;
   // variant 2 (small CTAs): register bound for two CTAs per SM where the
   // shared memory of two tiles lets two fit (the FP32 filter table of the x
-  // pass may still keep that pass at one)
+  // pass may still keep that pass at one); variant 1 of the large radices:
+  // as many CTAs as the tiles' shared memory allows, up to three
   static constexpr int SMEM_EST = 128 + 2 * N * B * CB;
-  static constexpr int MINB = (V == 2 && THREADS <= 256 && 2 * SMEM_EST <= 227 * 1024) ? 2 : 1;
+  static constexpr int min_blocks() {
+    if (BIG && V == 1) {  // the x pass's filter table (about 11 KB) may still cost one
+      const int by_smem = (228 * 1024) / (SMEM_EST + 1024);
+      return by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
+    }
+    return (V == 2 && THREADS <= 256 && 2 * SMEM_EST <= 227 * 1024) ? 2 : 1;
+  }
+  static constexpr int MINB = min_blocks();
   static constexpr int REG_BUDGET =
       65536 / (THREADS * MINB) < 255 ? 65536 / (THREADS * MINB) : 255;
   static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
-  static constexpr bool SPILL = REG_NEED > REG_BUDGET;
+  static constexpr bool SPILL = (BIG && V == 1) || REG_NEED > REG_BUDGET;
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
 };
 
@@ -354,12 +522,12 @@ template <typename R, int N, int V> struct AxisPolicy {
 // variant 3 the lines of variant 1 with warp barriers.
 template <typename R, int N, int V> struct ZPolicy {
   static constexpr int M = N / 2;
-  static constexpr int E = elems(M);
+  static constexpr int E = elems(skey<R>(M));
   static constexpr int P = M / E;
   static constexpr int CB = 2 * (int)sizeof(R);
   static constexpr int LD = M + (M >> 4) + 1;  // tile sizing (the widest padding)
   // the forward's last two and the inverse's first two stages in registers
-  static constexpr bool FUSE = fuse_pair<M, E>();
+  static constexpr bool FUSE = fuse_pair<R, M, E>();
   // Padding of the work tile, per direction: one empty slot every PAD values
   // (0: none). Chosen by counting the shared-memory wavefronts of every
   // stage's stores and loads for each size; FP32 (FP64 keeps 1 in 16).

@@ -36,15 +36,16 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
   using C = Cx<R>;
   constexpr bool FWD = MODE != kAxisInv, INV = MODE != kAxisFwd;
   using Pol = ct::AxisPolicy<R, N, V>;
-  constexpr int B = Pol::B, E = Pol::E, P = Pol::P, HALF = N / 2, S = ct::nstages(N);
+  constexpr int K = ct::skey<R>(N);
+  constexpr int B = Pol::B, E = Pol::E, P = Pol::P, HALF = N / 2, S = ct::nstages(K);
   constexpr int TILE = N * B;
   constexpr int TILE_STRIDE = (int)(((TILE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
   constexpr int INNER = HALF / B;
-  constexpr int RH = ct::radix_of(N, 0, true);  // radix at the register hand-off
-  static_assert(RH == ct::radix_of(N, S - 1, false), "hand-off radix");
+  constexpr int RH = ct::radix_of(K, 0, true);  // radix at the register hand-off
+  static_assert(RH == ct::radix_of(K, S - 1, false), "hand-off radix");
   constexpr int SPAN = N / RH, NB = E / RH;
   constexpr bool SPILL = Pol::SPILL;
-  constexpr bool FUSE = ct::fuse_pair<N, E>();  // stage pairs around the hand-off in registers
+  constexpr bool FUSE = ct::fuse_pair<R, N, E>();  // stage pairs around the hand-off in registers
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
@@ -284,8 +285,9 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD_INV, PAD = Pol::PAD_INV;
-  constexpr int S = ct::nstages(M);
-  constexpr int RL = ct::radix_of(M, S - 1, true), SPANL = M / RL, NBL = E / RL;
+  constexpr int KM = ct::skey<R>(M);
+  constexpr int S = ct::nstages(KM);
+  constexpr int RL = ct::radix_of(KM, S - 1, true), SPANL = M / RL, NBL = E / RL;
   constexpr int DENSE_STRIDE = (int)(((Pol::DENSE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
       const C z = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
       if constexpr (Pol::FUSE) {  // k = p + P*(b + (E/RA)*r): the first stage's layout
-        constexpr int RA = ct::radix_of(M, 0, true), NBA = E / RA;
+        constexpr int RA = ct::radix_of(KM, 0, true), NBA = E / RA;
         v[(i % NBA) * RA + i / NBA] = z;
       } else {
         st_w(k, z);
@@ -424,7 +426,8 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD_FWD, PAD = Pol::PAD_FWD;
-  constexpr int S = ct::nstages(M);
+  constexpr int KM = ct::skey<R>(M);
+  constexpr int S = ct::nstages(KM);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C *work = reinterpret_cast<C *>(smem_raw);
   const int tid = threadIdx.x;
@@ -464,7 +467,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     auto st_w = [&](int n, C v) { work[zpad<LD, PAD>(l, n)] = v; };
     if constexpr (Pol::FUSE) {  // the last two stages in registers, stored in natural order
       ct::stages<R, M, E, false, 0, S - 2, Pol::SY>(p, tw_half, ld_w, st_w);
-      constexpr int RB = ct::radix_of(M, S - 1, false), NBB = E / RB, SPANB = M / RB;
+      constexpr int RB = ct::radix_of(KM, S - 1, false), NBB = E / RB, SPANB = M / RB;
       C v[E];
       ct::last_two_stages_regs<R, M, E>(p, tw_half, ld_w, v);
       ct::stage_barrier<Pol::SY>();

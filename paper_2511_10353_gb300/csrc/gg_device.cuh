@@ -70,11 +70,53 @@ __device__ __forceinline__ uint4 noise_words(uint64_t seed, uint64_t group) {
 // u_a = (r_a + 1) 2^-32 in (0, 1], u_b = r_b 2^-32; rho = sqrt(-2 ln u_a);
 // outputs rho cos(2 pi u_b), rho sin(2 pi u_b). gauss4 applies it to the
 // pairs (r0, r1) and (r2, r3) of a group.
+//
+// FP32 form, built from the integer words so that each step keeps FP32
+// accuracy where the value is small:
+// * ln u_a: 1 - u_a = v = (2^32 - 1 - r_a) 2^-32 is exact in integers; for
+//   v < 2^-8 the series ln(1 - v) = -(v + v^2/2 + v^3/3 + v^4/4) (next term
+//   below 2^-34 v); otherwise log2 u_a from the hardware base-2 logarithm
+//   (absolute error below 2^-22.6 on [1/2, 2], two ulp elsewhere) times ln 2;
+// * rho = a rsqrt(a), a = -2 ln u_a (0 when u_a = 1);
+// * the angle 2 pi u_b is reduced exactly in integers to the nearest
+//   quarter turn q and a remainder x in [-pi/4, pi/4), sin x and cos x are
+//   their Taylor series to x^9 and x^10 (truncation below 2e-9), and the
+//   quarter turn is applied by swaps and signs.
+// Against the FP64 form: relative L2 about 1e-7, largest difference about
+// 1e-6 (the pair's cos/sin rounding, and near u_a = 1 the FP32 rounding of
+// a tiny rho).
+__device__ __forceinline__ float ln_u32(uint32_t ra) {
+  const uint32_t nv = ~ra;  // (1 - u_a) 2^32
+  if (nv < (1u << 24)) {
+    const float v = __uint2float_rn(nv) * 0x1p-32f;  // exact: nv < 2^24
+    return -v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 0.333333333f), 0.5f), 1.0f);
+  }
+  return __log2f(fmaf(__uint2float_rn(ra), 0x1p-32f, 0x1p-32f)) * 0.693147180559945309f;
+}
+__device__ __forceinline__ void sincos_turn32(uint32_t rb, float &s, float &c) {
+  const uint32_t q = (rb + (1u << 29)) >> 30;    // nearest quarter turn (mod 4)
+  const int32_t t = (int32_t)(rb - (q << 30));   // remainder, |t| <= 2^29 (an eighth)
+  const float x = (float)t * (6.28318530717958648f * 0x1p-32f);
+  const float x2 = x * x;
+  float sp = fmaf(x2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
+  sp = fmaf(x2, sp, 8.33333333e-3f);                      // 1/5!
+  sp = fmaf(x2, sp, -1.66666667e-1f);                     // -1/3!
+  const float sn = fmaf(x * x2, sp, x);
+  float cp = fmaf(x2, -2.75573192e-7f, 2.48015873e-5f);   // -1/10!, 1/8!
+  cp = fmaf(x2, cp, -1.38888889e-3f);                     // -1/6!
+  cp = fmaf(x2, cp, 4.16666667e-2f);                      // 1/4!
+  cp = fmaf(x2, cp, -0.5f);
+  const float cs = fmaf(x2, cp, 1.0f);
+  // sin(x + q pi/2), cos(x + q pi/2)
+  const float a = (q & 1) ? cs : sn, b = (q & 1) ? sn : cs;
+  s = (q & 2) ? -a : a;
+  c = ((q + 1) & 2) ? -b : b;
+}
 __device__ __forceinline__ void gauss2(uint32_t ra, uint32_t rb, float &c, float &s) {
-  const float ua = fmaf(__uint2float_rn(ra), 0x1p-32f, 0x1p-32f);
-  const float rho = sqrtf(-2.0f * logf(ua));
+  const float a = -2.0f * ln_u32(ra);
+  const float rho = a > 0.0f ? a * rsqrtf(a) : 0.0f;
   float sn, cs;
-  sincospif(2.0f * (__uint2float_rn(rb) * 0x1p-32f), &sn, &cs);
+  sincos_turn32(rb, sn, cs);
   c = rho * cs;
   s = rho * sn;
 }
