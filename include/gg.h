@@ -245,6 +245,25 @@ gg_status gg_batch_run(gg_batch_t *batch, const uint64_t *seeds, void *const *ps
 /* Wait for the last gg_batch_run; return the first device error. */
 gg_status gg_batch_sync(gg_batch_t *batch);
 
+/* Schedule of later gg_batch_run calls: on = 0 (default) one launch per pass
+ * and group as above; on = 1 the whole batch as ONE persistent launch
+ * (captured in the graph after the staging copies and a clear of its
+ * counters). Its CTAs take work items (pass, group, tile), numbered
+ * pass-major, from a device counter; a tile starts once its realization has
+ * completed every tile of the pass it reads (per-realization pass counters)
+ * and then counts itself done. Every wait is bounded (two seconds, then
+ * GG_ETIMEOUT from gg_batch_sync). Same butterflies as the per-pass launches
+ * (bit-identical results: only the tile shape differs). A work item is a
+ * run of consecutive tiles of one pass and realization (the bodies
+ * double-buffer their copies across it): on = 1 takes runs of up to 64
+ * tiles, on = 2, 4, ..., 256 runs of up to that many (single tiles cost
+ * 1.7x, 64-tile runs match the per-pass launches on the 48-realization
+ * workload). Requires FP32
+ * realizations of N = 64, 128, 192, 256 or 384 in at most 4 parameter groups
+ * (else GG_EINVAL); allocates the counters (64 + 8 * count words) on first
+ * use. Waits for a previous run and drops the captured graph. */
+gg_status gg_batch_set_persistent(gg_batch_t *batch, int on);
+
 /* Number of groups and total cells of the batch. */
 gg_status gg_batch_info(const gg_batch_t *batch, int *groups, int64_t *cells);
 

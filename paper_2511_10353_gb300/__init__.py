@@ -113,6 +113,7 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int64)]),
     "gg_batch_free": (None, [ctypes.c_void_p]),
     "gg_batch_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "gg_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gg_zeldovich_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_smooth": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -623,6 +624,13 @@ class Batch:
 
     def sync(self):
         _check(lib().gg_batch_sync(self._h))
+
+    def set_persistent(self, on=True, chunk=None):
+        """Later runs as one persistent launch over every pass and realization
+        (FP32, N in 64..384), or one launch per pass and group (the default).
+        chunk: most tiles per work item (a power of two up to 256; default 64)."""
+        v = (int(chunk) if chunk else 1) if on else 0
+        _check(lib().gg_batch_set_persistent(self._h, v))
 
     def launches(self):
         """Kernels one run launches (kernel nodes of the captured graph)."""

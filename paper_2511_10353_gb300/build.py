@@ -32,6 +32,7 @@ SOURCES = [
     "gg_kernels_f64.cu",
     "gg_kernels_common.cu",
     "gg_static.cu",
+    "gg_persist.cu",
     "gg_cic.cu",
     "gg_refine.cu",
     "gg_merge.cu",

@@ -123,6 +123,11 @@ struct gg_batch {
   cudaGraphExec_t exec = nullptr;
   uint32_t signature = 0;  // which (output, component) pairs the graph writes
   bool ran = false;
+  // one persistent launch for the whole batch (gg_batch_set_persistent)
+  bool persistent = false;
+  int persist_chunk = 0;             // most tiles per work item (0: the default)
+  unsigned int *counters = nullptr;  // device: work queue, abort flag, pass counters
+  int persist_blocks = 0;
 };
 
 namespace {
@@ -1090,111 +1095,175 @@ bool same_params(const gg_params &a, const gg_params &b) {
 
 // All passes of one group, on stream s, every launch covering all nb
 // realizations (captured into the batch's graph).
+// Arguments of the batched passes of one group (every realization of the
+// group in each launch): z forward, y forward, x fused, the two y inverse
+// passes, and the z inverse passes of the components some realization wants.
+template <typename R>
+void group_args(gg_batch::Group &g, uint32_t sig, gg::ZFwdArgs &z, gg::AxisArgs ax[4],
+                gg::ZInvArgs zi[3], bool on[3]) {
+  gg_plan_t *plan = g.plan;
+  const int n = (int)plan->p.n, half = n / 2;
+  const int nb = (int)g.members.size();
+  const int64_t grid_c = (int64_t)n * n * half;  // complex values per realization
+  z = gg::ZFwdArgs{};
+  z.out = g.work[0];
+  z.nlines = (int64_t)nb * n * n;
+  z.lines_per_real = (int64_t)n * n;
+  z.seeds = g.d_seeds;
+  z.n = n;
+  z.lines_per_cta = plan->z_lines;
+  z.st = plan->st_half;
+  z.tw_half = plan->tab.tw_half;
+  z.tw_full = plan->tab.tw_n;
+  z.variant = plan->variant[0];
+  auto axb = [&](const void *src) {
+    gg::AxisArgs c = axis_args<R>(plan, 1, src);
+    c.nbatch = nb;
+    c.batch_stride = grid_c;
+    return c;
+  };
+  gg::AxisArgs &y = ax[0];
+  y = axb(g.work[0]);
+  y.fwd = 1;
+  y.nout = 1;
+  y.dst[0] = g.work[0];
+  y.variant = plan->variant[1];
+  gg::AxisArgs &x = ax[1];
+  x = axb(g.work[0]);
+  x.axis = 0;
+  x.stride = (int64_t)n * half;
+  x.outer_stride = half;
+  x.fwd = 1;
+  x.inv = 1;
+  x.pre = 1;
+  x.table = plan->tab.u_phi;
+  x.interp = plan->tab.interp_u;
+  x.interp_cells = plan->tab.interp_cells;
+  x.nout = 2;
+  x.dst[0] = g.work[0];
+  x.mul[0] = gg::kMulIm;
+  x.dst[1] = g.work[1];
+  x.mul[1] = gg::kMulNone;
+  x.variant = plan->variant[2];
+  gg::AxisArgs &ya = ax[2];
+  ya = axb(g.work[0]);
+  ya.inv = 1;
+  ya.nout = 1;
+  ya.dst[0] = g.work[0];
+  ya.variant = plan->variant[3];
+  gg::AxisArgs &yb = ax[3];
+  yb = axb(g.work[1]);
+  yb.inv = 1;
+  yb.nout = 2;
+  yb.dst[0] = g.work[1];
+  yb.mul[0] = gg::kMulIm;
+  yb.dst[1] = g.work[2];
+  yb.mul[1] = gg::kMulNone;
+  yb.variant = plan->variant[4];
+  for (int j = 0; j < 3; ++j) {
+    on[j] = (sig >> j) & 0x49;  // psi_j, pos_j or vel_j wanted anywhere
+    gg::ZInvArgs &zj = zi[j];
+    zj = gg::ZInvArgs{};
+    zj.src = g.work[j];
+    zj.nlines = (int64_t)nb * n * n;
+    zj.lines_per_real = (int64_t)n * n;
+    zj.psi_list = ((sig >> (0 * 3 + j)) & 1) ? g.d_lists + (0 * 3 + j) * nb : nullptr;
+    zj.pos_list = ((sig >> (1 * 3 + j)) & 1) ? g.d_lists + (1 * 3 + j) * nb : nullptr;
+    zj.vel_list = ((sig >> (2 * 3 + j)) & 1) ? g.d_lists + (2 * 3 + j) * nb : nullptr;
+    zj.lists_full = ((sig >> (9 + 1 * 3 + j)) & 1) && ((sig >> (9 + 2 * 3 + j)) & 1);
+    zj.n = n;
+    zj.lines_per_cta = plan->z_lines;
+    zj.comp = j;
+    zj.mul_kz = j == 2;
+    zj.box = plan->p.box;
+    zj.cell = plan->p.box / (double)n;
+    zj.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
+    zj.vfac = plan->info.vfac;
+    zj.st = plan->st_half;
+    zj.tw_half = plan->tab.tw_half;
+    zj.tw_full = plan->tab.tw_n;
+    zj.err = plan->err;
+    zj.variant = plan->variant[5];
+  }
+}
+
+// The group's seeds and output lists, staged in pinned memory, to the device.
+cudaError_t group_staging(gg_batch::Group &g, cudaStream_t s) {
+  const int nb = (int)g.members.size();
+  cudaError_t e = cudaMemcpyAsync(g.d_seeds, g.h_seeds, sizeof(uint64_t) * nb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g.d_lists, g.h_lists, sizeof(void *) * 9 * nb, cudaMemcpyHostToDevice, s);
+  return e;
+}
+
 template <typename R>
 gg_status group_passes(gg_batch::Group &g, cudaStream_t s, uint32_t sig) {
   gg_plan_t *plan = g.plan;
   const cudaStream_t saved = plan->stream;
   plan->stream = s;
-  const int n = (int)plan->p.n, half = n / 2;
-  const int nb = (int)g.members.size();
-  const int64_t grid_c = (int64_t)n * n * half;  // complex values per realization
+  const int n = (int)plan->p.n;
   gg_status st = GG_OK;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(g.d_seeds, g.h_seeds, sizeof(uint64_t) * nb, cudaMemcpyHostToDevice, s)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(g.d_lists, g.h_lists, sizeof(void *) * 9 * nb, cudaMemcpyHostToDevice, s)) !=
-          cudaSuccess) {
+  if ((e = group_staging(g, s)) != cudaSuccess) {
     plan->stream = saved;
     return cuda_fail(nullptr, e, "batch staging copies");
   }
+  gg::ZFwdArgs z;
+  gg::AxisArgs ax[4];
+  gg::ZInvArgs zi[3];
+  bool on[3];
+  group_args<R>(g, sig, z, ax, zi, on);
+  const int kinds[4] = {kYFwd, kXFused, kYInvX, kYInvYZ};
+  const char *const what[4] = {"batched y forward", "batched x fused", "batched y inverse (x)",
+                               "batched y inverse (y/z)"};
   do {
-    gg::ZFwdArgs z{};
-    z.out = g.work[0];
-    z.nlines = (int64_t)nb * n * n;
-    z.lines_per_real = (int64_t)n * n;
-    z.seeds = g.d_seeds;
-    z.n = n;
-    z.lines_per_cta = plan->z_lines;
-    z.st = plan->st_half;
-    z.tw_half = plan->tab.tw_half;
-    z.tw_full = plan->tab.tw_n;
-    z.variant = plan->variant[0];
     e = gg::spec_has<R>(n) ? gg::spec_zfwd<R>(z, s) : gg::launch_zfwd<R>(z, s);
     if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "batched z forward"); break; }
-    auto ax = [&](const void *src) {
-      gg::AxisArgs c = axis_args<R>(plan, 1, src);
-      c.nbatch = nb;
-      c.batch_stride = grid_c;
-      return c;
-    };
-    gg::AxisArgs y = ax(g.work[0]);
-    y.fwd = 1;
-    y.nout = 1;
-    y.dst[0] = g.work[0];
-    y.variant = plan->variant[1];
-    if ((st = launch_axis_timed<R>(plan, y, kYFwd, "batched y forward")) != GG_OK) break;
-    gg::AxisArgs x = ax(g.work[0]);
-    x.axis = 0;
-    x.stride = (int64_t)n * half;
-    x.outer_stride = half;
-    x.fwd = 1;
-    x.inv = 1;
-    x.pre = 1;
-    x.table = plan->tab.u_phi;
-    x.interp = plan->tab.interp_u;
-    x.interp_cells = plan->tab.interp_cells;
-    x.nout = 2;
-    x.dst[0] = g.work[0];
-    x.mul[0] = gg::kMulIm;
-    x.dst[1] = g.work[1];
-    x.mul[1] = gg::kMulNone;
-    x.variant = plan->variant[2];
-    if ((st = launch_axis_timed<R>(plan, x, kXFused, "batched x fused")) != GG_OK) break;
-    gg::AxisArgs ya = ax(g.work[0]);
-    ya.inv = 1;
-    ya.nout = 1;
-    ya.dst[0] = g.work[0];
-    ya.variant = plan->variant[3];
-    if ((st = launch_axis_timed<R>(plan, ya, kYInvX, "batched y inverse (x)")) != GG_OK) break;
-    gg::AxisArgs yb = ax(g.work[1]);
-    yb.inv = 1;
-    yb.nout = 2;
-    yb.dst[0] = g.work[1];
-    yb.mul[0] = gg::kMulIm;
-    yb.dst[1] = g.work[2];
-    yb.mul[1] = gg::kMulNone;
-    yb.variant = plan->variant[4];
-    if ((st = launch_axis_timed<R>(plan, yb, kYInvYZ, "batched y inverse (y/z)")) != GG_OK) break;
+    for (int k = 0; k < 4 && st == GG_OK; ++k) st = launch_axis_timed<R>(plan, ax[k], kinds[k], what[k]);
     for (int j = 0; j < 3 && st == GG_OK; ++j) {
-      const bool any = (sig >> j) & 0x49;  // psi_j, pos_j or vel_j wanted anywhere
-      if (!any) continue;
-      gg::ZInvArgs zi{};
-      zi.src = g.work[j];
-      zi.nlines = (int64_t)nb * n * n;
-      zi.lines_per_real = (int64_t)n * n;
-      zi.psi_list = ((sig >> (0 * 3 + j)) & 1) ? g.d_lists + (0 * 3 + j) * nb : nullptr;
-      zi.pos_list = ((sig >> (1 * 3 + j)) & 1) ? g.d_lists + (1 * 3 + j) * nb : nullptr;
-      zi.vel_list = ((sig >> (2 * 3 + j)) & 1) ? g.d_lists + (2 * 3 + j) * nb : nullptr;
-      zi.lists_full = ((sig >> (9 + 1 * 3 + j)) & 1) && ((sig >> (9 + 2 * 3 + j)) & 1);
-      zi.n = n;
-      zi.lines_per_cta = plan->z_lines;
-      zi.comp = j;
-      zi.mul_kz = j == 2;
-      zi.box = plan->p.box;
-      zi.cell = plan->p.box / (double)n;
-      zi.q_offset = (plan->p.flags & GG_Q_CORNER) ? 0.0 : 0.5;
-      zi.vfac = plan->info.vfac;
-      zi.st = plan->st_half;
-      zi.tw_half = plan->tab.tw_half;
-      zi.tw_full = plan->tab.tw_n;
-      zi.err = plan->err;
-      zi.variant = plan->variant[5];
-      e = gg::spec_has<R>(n) ? gg::spec_zinv<R>(zi, s) : gg::launch_zinv<R>(zi, s);
+      if (!on[j]) continue;
+      e = gg::spec_has<R>(n) ? gg::spec_zinv<R>(zi[j], s) : gg::launch_zinv<R>(zi[j], s);
       if (e != cudaSuccess) st = cuda_fail(nullptr, e, "batched z inverse");
     }
   } while (false);
   plan->stream = saved;
   return st;
+}
+
+// The whole batch as one persistent launch (gg_persist.cu): staging copies
+// of every group, the pass counters cleared, then the kernel.
+gg_status persist_passes(gg_batch_t *b, cudaStream_t s, uint32_t sig) {
+  gg::PersistPlan pp{};
+  pp.ngroups = (int)b->groups.size();
+  pp.realizations = b->count;
+  pp.counters = b->counters;
+  pp.err = b->groups[0].plan->err;
+  pp.chunk = b->persist_chunk;
+  cudaError_t e;
+  int first = 0;
+  for (int gi = 0; gi < pp.ngroups; ++gi) {
+    gg_batch::Group &g = b->groups[gi];
+    if ((e = group_staging(g, s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch staging copies");
+    gg::PersistGroupArgs &pg = pp.g[gi];
+    bool on[3];
+    group_args<float>(g, sig, pg.zf, pg.ax, pg.zi, on);
+    pg.n = (int)g.plan->p.n;
+    pg.nb = (int)g.members.size();
+    pg.first = first;
+    first += pg.nb;
+    for (int j = 0; j < 3; ++j) pg.zi_on[j] = on[j] ? 1 : 0;
+    // the pos + vel instantiation when every realization wants both, no psi
+    const bool lists_full = (((sig >> 9) >> 3) & 7) == 7 && (((sig >> 9) >> 6) & 7) == 7;
+    pg.plain = lists_full && (sig & 7) == 0 ? 1 : 0;
+    for (int j = 0; j < 3; ++j) pg.zi[j].err = pp.err;
+    for (auto &a : pg.ax) a.err = pp.err;
+  }
+  const size_t words = 64 + (size_t)8 * b->count;
+  if ((e = cudaMemsetAsync(b->counters, 0, words * sizeof(unsigned), s)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "clearing the pass counters");
+  if ((e = gg::launch_persist(pp, s, &b->persist_blocks)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "persistent batched launch");
+  return GG_OK;
 }
 
 void batch_release(gg_batch_t *b) {
@@ -1214,6 +1283,7 @@ void batch_release(gg_batch_t *b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->counters) cudaFree(b->counters);
 }
 
 }  // namespace
@@ -1795,8 +1865,10 @@ gg_status gg_batch_run(gg_batch_t *b, const uint64_t *seeds, void *const *psi, v
     if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(nullptr, e, "cudaStreamBeginCapture (a batch needs a non-default stream)");
     gg_status st = GG_OK;
-    if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) st = cuda_fail(nullptr, e, "fork");
+    if (b->persistent) st = persist_passes(b, b->stream, sig);
+    else if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) st = cuda_fail(nullptr, e, "fork");
     for (auto &g : b->groups) {
+      if (b->persistent) break;
       if (st != GG_OK) break;
       if ((e = cudaStreamWaitEvent(g.s, b->fork, 0)) != cudaSuccess) {
         st = cuda_fail(nullptr, e, "fork wait");
@@ -1844,6 +1916,38 @@ gg_status gg_batch_info(const gg_batch_t *b, int *groups, int64_t *cells) {
   if (!b) return fail(nullptr, GG_EINVAL, "batch is NULL");
   if (groups) *groups = (int)b->groups.size();
   if (cells) *cells = b->cells;
+  return GG_OK;
+}
+
+gg_status gg_batch_set_persistent(gg_batch_t *b, int on) {
+  if (!b) return fail(nullptr, GG_EINVAL, "batch is NULL");
+  if (on < 0 || on > 256 || (on > 1 && (on & (on - 1))))
+    return fail(nullptr, GG_EINVAL, "on: 0, 1 or a power of two up to 256 (tiles per work item)");
+  if (on) {
+    if ((int)b->groups.size() > gg::kPersistMaxGroups)
+      return fail(nullptr, GG_EINVAL, "persistent form: at most 4 parameter groups");
+    for (auto &g : b->groups)
+      if (g.plan->real_bytes != 4 || !gg::persist_has((int)g.plan->p.n))
+        return fail(nullptr, GG_EINVAL, "persistent form: FP32 grids of N = 64, 128, 192, 256, 384 only");
+    if (!b->counters) {
+      const size_t words = 64 + (size_t)8 * b->count;
+      if (cudaMalloc(&b->counters, words * sizeof(unsigned)) != cudaSuccess) {
+        b->counters = nullptr;
+        return fail(nullptr, GG_ENOMEM, "cudaMalloc of the pass counters failed");
+      }
+    }
+  }
+  cudaError_t e;
+  if (b->ran && (e = cudaEventSynchronize(b->done)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "waiting for the previous batch run");
+  if (b->exec) {  // the next gg_batch_run captures the other schedule
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  b->persistent = on != 0;
+  b->persist_chunk = on > 1 ? on : 0;
   return GG_OK;
 }
 

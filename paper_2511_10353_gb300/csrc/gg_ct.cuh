@@ -476,18 +476,23 @@ __device__ __forceinline__ void inverse_head_store(int p, const Cx<R> *v, const 
 // Whether the handed-off spectrum may stay in registers while an inverse
 // runs is estimated from the register budget; otherwise (SPILL) it is parked
 // in shared memory and every output reads it from there.
+// Tile variant of the persistent batched kernel (gg_persist.cu): exactly 256
+// threads per CTA for every pass and size, two CTAs per SM.
+constexpr int kPersistV = 4;
+
 template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int CB = 2 * (int)sizeof(R);
   static constexpr bool BIG = is_big(skey<R>(N));
   static constexpr int E0 = elems(skey<R>(N));
   static constexpr bool DOUBLE_OK = N % (2 * E0) == 0 && 2 * E0 * ((int)sizeof(R) / 4) <= 16;
-  static constexpr int E = (V >= 1 && DOUBLE_OK) ? 2 * E0 : E0;
+  static constexpr int E = ((V == 1 || V == 2) && DOUBLE_OK) ? 2 * E0 : E0;
   static constexpr int P = N / E;
   // large-radix schedules (E cannot double): variant 1 is the small tile of
   // variant 2 with the handed-off spectrum parked in shared memory, so that
   // three CTAs' registers fit an SM
   static constexpr bool SMALL = V == 2 || (BIG && V == 1);
   static constexpr int pick() {
+    if (V == kPersistV) return 256 / P;  // the persistent batched kernel: 256 threads
     int b = 128 / CB;
     while (b > 1 && ((N / 2) % b != 0 || P * b > 512 || 2 * (N * b * CB) > 200 * 1024)) b /= 2;
     if (SMALL && b * CB > 32) b /= 2;
@@ -501,6 +506,7 @@ template <typename R, int N, int V> struct AxisPolicy {
   // as many CTAs as the tiles' shared memory allows, up to three
   static constexpr int SMEM_EST = 128 + 2 * N * B * CB;
   static constexpr int min_blocks() {
+    if (V == kPersistV) return 2;
     if (BIG && V == 1) {  // the x pass's filter table (about 11 KB) may still cost one
       const int by_smem = (228 * 1024) / (SMEM_EST + 1024);
       return by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
@@ -513,6 +519,7 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
   static constexpr bool SPILL = (BIG && V == 1) || REG_NEED > REG_BUDGET;
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
+  static_assert(V != kPersistV || (THREADS == 256 && (N / 2) % B == 0), "persistent tile");
 };
 
 // z passes: lines per tile, variant 0 ~256 threads (sized so that two dense
@@ -545,6 +552,7 @@ template <typename R, int N, int V> struct ZPolicy {
   static constexpr int LD_INV = M + (PAD_INV ? M / PAD_INV : 0) + 1;
   static constexpr int LD_FWD = M + (PAD_FWD ? M / PAD_FWD : 0) + 1;
   static constexpr int pick() {
+    if (V == kPersistV) return 256 / P;  // the persistent batched kernel: 256 threads
     int l = 1;
     while (l < 64 && P * l * 2 <= 256 && (2 * (2 * l) * M + 2 * l * LD) * CB <= 160 * 1024) l *= 2;
     if ((V == 1 || V == 3) && l > 1) l /= 2;
@@ -563,6 +571,7 @@ template <typename R, int N, int V> struct ZPolicy {
   // staging tile and the padded tile; forward: the padded tile). FP64 lines
   // need twice the registers and run at the FP64 rate: no bound there.
   static constexpr int min_blocks(int smem) {
+    if (V == kPersistV) return 2;
     const int by_smem = (228 * 1024) / smem, by_warps = 512 / THREADS;
     const int m = by_smem < by_warps ? by_smem : by_warps;
     return sizeof(R) == 4 && m > 0 ? m : 1;

@@ -30,9 +30,13 @@ __device__ __forceinline__ int ct_freq(int n, int N) { return n < (N >> 1) ? n :
 // interpolated FP32 table at a.interp (the fused x pass of the plain path).
 constexpr int kAxisFwd = 1, kAxisInv = 2, kAxisFwdInv = 3;
 constexpr int kFiltArgs = 0, kFiltNone = 1, kFiltInterp = 2;
+// The body processes tiles t0, t0 + tstep, ... below tlimit (the kernel: its
+// CTA's share of all tiles; the persistent batched kernel: one tile). It
+// returns false when a copy wait gave up (the error word then holds
+// GG_ETIMEOUT). `map` must live in parameter (grid-constant) memory.
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
-__global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
-    k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
+__device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs &a, int64_t t0,
+                                          int64_t tstep, int64_t tlimit) {
   using C = Cx<R>;
   constexpr bool FWD = MODE != kAxisInv, INV = MODE != kAxisFwd;
   using Pol = ct::AxisPolicy<R, N, V>;
@@ -89,13 +93,14 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
   // late: one input buffer (0) and one work buffer (1); the copy of the next
   // tile is issued during the last output
   const bool late = SPILL && INV && a.nout > 1;
-  int64_t t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
-  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+  if (tlimit > ntiles) tlimit = ntiles;
+  int64_t t = t0;
+  if (tid == 0 && t < tlimit) issue(t, 0);
+  for (int it = 0; t < tlimit; t += tstep, ++it) {
     const int sb = late ? 0 : it & 1;
     const uint32_t phase = late ? (uint32_t)(it & 1) : (uint32_t)((it >> 1) & 1);
-    const int64_t tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles && !late) {
+    const int64_t tn = t + tstep;
+    if (tid == 0 && tn < tlimit && !late) {
       fence_proxy_async_smem();
       issue(tn, sb ^ 1);
     }
@@ -126,9 +131,9 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     }
     const bool ok = __syncthreads_and(mbar_wait(&bars[sb], phase, a.err, a.wait_us));
     if (!ok) {  // late: no other copy is in flight
-      if (tid == 0 && tn < ntiles && !late && !a.test_skip_copy)
+      if (tid == 0 && tn < tlimit && !late && !a.test_skip_copy)
         mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr, a.wait_us);
-      return;
+      return false;
     }
     auto ld_smem = [&](int n) { return buf[n * B + c]; };
     auto st_smem = [&](int n, C v) { buf[n * B + c] = v; };
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
       // the previous output's last stage has read the work buffer; SPILL with
       // one buffer: every thread has read its parked spectrum
       if (o > 0 || (SPILL && !late)) __syncthreads();
-      if (late && o == a.nout - 1 && tid == 0 && tn < ntiles) {  // the input buffer is free
+      if (late && o == a.nout - 1 && tid == 0 && tn < tlimit) {  // the input buffer is free
         fence_proxy_async_smem();
         issue(tn, 0);
       }
@@ -253,6 +258,18 @@ __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPoli
     }
     __syncthreads();
   }
+  __syncthreads();
+  if (tid == 0) {  // the caller may reuse the shared memory
+    mbar_inval(&bars[0]);
+    mbar_inval(&bars[1]);
+  }
+  return true;
+}
+
+template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
+__global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
+    k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
+  axis_body<R, N, V, MODE, CUT, FILT>(map, a, blockIdx.x, gridDim.x, INT64_MAX);
 }
 
 // ------------------------------------------------------------ z passes
@@ -280,8 +297,8 @@ template <int LD, int PAD> __device__ __forceinline__ int zpad(int l, int n) {
 // per-realization lists, every entry set).
 constexpr int kZPosVel = 1, kZPosVelZ = 2;
 template <typename R, int N, int V, bool EXT = false, int OUT = 0>
-__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_INV)
-    k_zinv_ct(const ZInvArgs a) {
+__device__ __forceinline__ bool zinv_body(const ZInvArgs &a, int64_t t0, int64_t tstep,
+                                          int64_t tlimit) {
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD_INV, PAD = Pol::PAD_INV;
@@ -308,14 +325,15 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
               (uint32_t)(Pol::DENSE * sizeof(C)), bar);
   };
   const R box = (R)a.box, cell = (R)a.cell, qo = (R)a.q_offset, vfac = (R)a.vfac;
-  int64_t t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t);
-  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-    const int64_t tn = t + gridDim.x;
+  if (tlimit > ntiles) tlimit = ntiles;
+  int64_t t = t0;
+  if (tid == 0 && t < tlimit) issue(t);
+  for (int it = 0; t < tlimit; t += tstep, ++it) {
+    const int64_t tn = t + tstep;
     int l = tid / P, p = tid - (tid / P) * P;
     asm volatile("" : "+r"(l), "+r"(p));
     const bool ok = __syncthreads_and(mbar_wait(bar, (uint32_t)(it & 1), a.err));
-    if (!ok) return;  // nothing else in flight: the next copy is issued after this wait
+    if (!ok) return false;  // nothing else in flight: the next copy is issued after this wait
     const C *dl = dense + l * M;
     const R pf = (R)p;  // (R)(p + c) == pf + (R)c exactly: small integers
     auto ld_w = [&](int n) { return work[zpad<LD, PAD>(l, n)]; };
@@ -346,7 +364,7 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       ct::inverse_head_store<R, M, E>(p, v, st_w);
     }
     __syncthreads();
-    if (tid == 0 && tn < ntiles) {  // the dense buffer has been read: fetch the next block
+    if (tid == 0 && tn < tlimit) {  // the dense buffer has been read: fetch the next block
       fence_proxy_async_smem();
       issue(tn);
     }
@@ -415,14 +433,23 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
       }
     ct::stage_barrier<Pol::SY>();  // the work tile's lines are rewritten next tile
   }
+  __syncthreads();
+  if (tid == 0) mbar_inval(bar);  // the caller may reuse the shared memory
+  return true;
+}
+
+template <typename R, int N, int V, bool EXT = false, int OUT = 0>
+__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_INV)
+    k_zinv_ct(const ZInvArgs a) {
+  zinv_body<R, N, V, EXT, OUT>(a, blockIdx.x, gridDim.x, INT64_MAX);
 }
 
 // Forward z pass: Philox noise (or caller noise) of L lines into the padded
 // work tile, the length-N/2 transform in place, then the real-input unpacking
 // X_k = (Z_k + conj Z_{M-k})/2 - i/2 e^{-2 pi i k/N} (Z_k - conj Z_{M-k}).
 template <typename R, int N, int V>
-__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_FWD)
-    k_zfwd_ct(const ZFwdArgs a) {
+__device__ __forceinline__ void zfwd_body(const ZFwdArgs &a, int64_t t0, int64_t tstep,
+                                          int64_t tlimit) {
   using C = Cx<R>;
   using Pol = ct::ZPolicy<R, N, V>;
   constexpr int M = Pol::M, E = Pol::E, P = Pol::P, L = Pol::L, LD = Pol::LD_FWD, PAD = Pol::PAD_FWD;
@@ -434,7 +461,8 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
   const int64_t ntiles = a.nlines / L;
   const C *tw_half = reinterpret_cast<const C *>(a.tw_half);
   const C *twf = reinterpret_cast<const C *>(a.tw_full);
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  if (tlimit > ntiles) tlimit = ntiles;
+  for (int64_t t = t0; t < tlimit; t += tstep) {
     int l = tid / P, p = tid - (tid / P) * P;
     asm volatile("" : "+r"(l), "+r"(p));
     const int64_t line = t * L + l;
@@ -491,6 +519,12 @@ __global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, 
     }
     ct::stage_barrier<Pol::SY>();  // the work tile's lines are rewritten next tile
   }
+}
+
+template <typename R, int N, int V>
+__global__ void __launch_bounds__(ct::ZPolicy<R, N, V>::THREADS, ct::ZPolicy<R, N, V>::MINB_FWD)
+    k_zfwd_ct(const ZFwdArgs a) {
+  zfwd_body<R, N, V>(a, blockIdx.x, gridDim.x, INT64_MAX);
 }
 
 // ------------------------------------------------------------ launchers

@@ -224,6 +224,36 @@ constexpr int kSpecZVariants = 4;     // ... per z pass
 template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zinv(const ZInvArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zfwd(const ZFwdArgs &a, cudaStream_t s);
+// Persistent batched form (gg_persist.cu): every pass of every realization
+// of a batch in one launch. Work items (pass, group, tile) are taken in that
+// order from a device queue; a tile starts once its realization has
+// completed every tile of the pass it reads (per-realization pass counters,
+// bounded waits), then adds itself to its own pass's counter.
+constexpr int kPersistMaxGroups = 4;
+constexpr int kPersistPasses = 8;  // z fwd, y fwd, x fused, y inv (x), y inv (y/z), z inv x3
+struct PersistGroupArgs {
+  int n;                  // FP32, one of the sizes persist_has accepts
+  int nb;                 // realizations of the group
+  int first;              // index of its first realization in the pass counters
+  int plain;              // z inverse: every realization wants pos and vel (no psi)
+  int zi_on[3];           // which z inverse passes run
+  ZFwdArgs zf;
+  AxisArgs ax[4];         // y forward, x fused, y inverse (x branch), y inverse (y/z)
+  ZInvArgs zi[3];
+};
+struct PersistPlan {
+  int ngroups;
+  int realizations;       // summed over the groups
+  PersistGroupArgs g[kPersistMaxGroups];
+  unsigned int *counters; // device, 64 + 8 * realizations words, zeroed before each launch
+  int *err;               // device error word (2: a wait gave up)
+  uint32_t wait_us;       // limit of every wait (0: two seconds)
+  int chunk;              // most tiles per work item (a power of two; 0: 64)
+};
+bool persist_has(int n);
+// Fills the tile shapes and tensor maps and launches on s (capturable).
+cudaError_t launch_persist(PersistPlan p, cudaStream_t s, int *launched_blocks);
+
 // Message returned by gg_last_error(NULL) on this host thread.
 void set_thread_error(const char *msg);
 cudaError_t launch_noise_bits(uint64_t seed, int64_t first, int64_t count, uint32_t *out,

@@ -102,3 +102,90 @@ def test_batched_48_workload(gg):
             assert np.abs(d).max() < 4 * ulp + 1e-5 * np.abs(ora["psi"][j]).max(), (i, j)
         del ora
     b.close()
+
+
+def _equal_outputs(a, b, count):
+    for k in ("psi", "pos", "vel"):
+        for i in range(count):
+            for j in range(3):
+                x, y = a[k][i][j], b[k][i][j]
+                if x is None:
+                    continue
+                assert torch.equal(x, y), (k, i, j)
+
+
+def test_persistent_launch_equals_pass_launches(gg):
+    """The whole batch as one persistent launch (work items taken in order,
+    per-realization pass counters) computes the same butterflies as the
+    per-pass launches: bit-identical outputs, with new seeds on replay."""
+    specs = []
+    for i, n in enumerate((64, 128, 192, 384, 64, 128)):  # four parameter groups
+        specs.append(dict(n=n, box=float(n), cosmo=BBKS, z_init=50.0))
+    b = gg.Batch(specs)
+    ref = b.empty_outputs(psi=True)
+    got = b.empty_outputs(psi=True)
+    for seeds in ([1, 2, 3, 4, 5, 6], [11, 12, 13, 14, 15, 16]):
+        b.set_persistent(False)
+        b.run(seeds, ref)
+        b.sync()
+        b.set_persistent(True)
+        b.run(seeds, got)
+        b.sync()
+        assert b.launches() == 1
+        _equal_outputs(got, ref, len(specs))
+    b.close()
+
+
+def test_persistent_partial_outputs(gg):
+    """Partial outputs take the generic z inverse in the persistent launch."""
+    specs = [dict(n=128, box=128.0, cosmo=BBKS, z_init=50.0)] * 3
+    b = gg.Batch(specs)
+    b.set_persistent(True)
+    out = b.empty_outputs(psi=False, pos=True, vel=False)
+    out["pos"][1] = [None, out["pos"][1][1], None]
+    b.run([5, 6, 7], out)
+    b.sync()
+    want = _solo(gg, specs[1], 6)
+    assert np.array_equal(out["pos"][1][1].cpu().numpy(), want["pos"][1])
+    want0 = _solo(gg, specs[0], 5)
+    for j in range(3):
+        assert np.array_equal(out["pos"][0][j].cpu().numpy(), want0["pos"][j])
+    b.close()
+
+
+def test_persistent_48_workload_against_oracle(gg):
+    """The 48-realization workload as one persistent launch: bit-identical to
+    the per-pass launches, and its 384^3 member within FP32 parity of the
+    FP64 oracle."""
+    from paper_2511_10353_gb300.workloads import batched_realizations
+    from tests.gpu_helpers import min_image, rel_l2, run_oracle
+    specs = batched_realizations()
+    b = gg.Batch(specs)
+    seeds = [w["seed"] for w in specs]
+    ref = b.empty_outputs()
+    got = b.empty_outputs()
+    b.run(seeds, ref)
+    b.sync()
+    b.set_persistent(True)
+    b.run(seeds, got)
+    b.sync()
+    assert b.launches() == 1
+    _equal_outputs(got, ref, len(specs))
+    del ref
+    w = specs[7]  # 384^3, seed 8
+    ora = run_oracle(w, seed=seeds[7])
+    for j in range(3):
+        assert rel_l2(got["vel"][7][j].cpu().numpy(), ora["vel"][j]) < 1e-5, j
+        pos = got["pos"][7][j].cpu().numpy().astype(np.float64)
+        d = min_image(pos - ora["pos"][j], w["box"])
+        assert np.abs(d).max() < 4 * np.spacing(np.float32(w["box"])) + 1e-5 * np.abs(ora["psi"][j]).max()
+    b.close()
+
+
+def test_persistent_rejects_unsupported_batches(gg):
+    specs = [dict(n=48, box=48.0, cosmo=BBKS, z_init=50.0)]
+    b = gg.Batch(specs)
+    with pytest.raises(gg.GGError) as ex:
+        b.set_persistent(True)
+    assert ex.value.status == gg.GG_EINVAL
+    b.close()
