@@ -44,6 +44,8 @@ __host__ __device__ constexpr int big_radix(int n, int s) {
   switch (n) {
     case 256: return s < 2 ? 16 : 0;
     case 512: return s == 0 ? 32 : (s == 1 ? 16 : 0);
+    case 768: return s < 2 ? 8 : (s == 2 ? 12 : 0);
+    case 1536: return s < 2 ? 8 : (s == 2 ? 24 : 0);
     default: return 0;
   }
 }
@@ -545,7 +547,7 @@ template <typename R, int N, int V> struct ZPolicy {
       if (M == 192 || M == 96) return 64;
     }
     if (M == 96) return 32;           // N = 192: 1.2x / 1.5x the minimum instead of 2x
-    if (inv && M == 768) return 0;    // N = 1536 inverse: 1.25x instead of 1.48x
+    if (inv && M == 768) return 32;   // N = 1536 inverse (8 x 8 x 12, first stage in registers): 1.5x instead of 2x
     return 16;
   }
   static constexpr int PAD_INV = pad_of(true), PAD_FWD = pad_of(false);

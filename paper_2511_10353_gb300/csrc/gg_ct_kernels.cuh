@@ -305,6 +305,12 @@ __device__ __forceinline__ bool zinv_body(const ZInvArgs &a, int64_t t0, int64_t
   constexpr int KM = ct::skey<R>(M);
   constexpr int S = ct::nstages(KM);
   constexpr int RL = ct::radix_of(KM, S - 1, true), SPANL = M / RL, NBL = E / RL;
+  // stages of the inverse done in registers straight from the c2r
+  // pre-processing (which yields exactly the first stage's inputs): two
+  // where a thread holds whole butterflies of both, one for the 768-point
+  // lines (8 x 8 x 12: measured 8.35 -> 7.27 ms at N = 1536; at M = 256 the
+  // register-resident first stage was slower, 0.262 -> 0.282 ms)
+  constexpr int HEAD = Pol::FUSE ? 2 : (S >= 3 && M >= 768 ? 1 : 0);
   constexpr int DENSE_STRIDE = (int)(((Pol::DENSE * sizeof(C) + 127) / 128) * 128 / sizeof(C));
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
@@ -352,23 +358,31 @@ __device__ __forceinline__ bool zinv_body(const ZInvArgs &a, int64_t t0, int64_t
       const C s = {xk.x + xm.x, xk.y - xm.y};  // X_k + conj X_{M-k}
       const C d = {xk.x - xm.x, xk.y + xm.y};  // X_k - conj X_{M-k}
       const C z = cadd(s, mul_pi(cmulc(d, ldg_c(twf + k))));
-      if constexpr (Pol::FUSE) {  // k = p + P*(b + (E/RA)*r): the first stage's layout
+      if constexpr (HEAD > 0) {  // k = p + P*(b + (E/RA)*r): the first stage's layout
         constexpr int RA = ct::radix_of(KM, 0, true), NBA = E / RA;
         v[(i % NBA) * RA + i / NBA] = z;
       } else {
         st_w(k, z);
       }
     }
-    if constexpr (Pol::FUSE) {  // the inverse's first two stages in registers
+    if constexpr (HEAD == 2) {  // the inverse's first two stages in registers
       ct::inverse_head_regs<R, M, E>(tw_half, v);
       ct::inverse_head_store<R, M, E>(p, v, st_w);
+    } else if constexpr (HEAD == 1) {  // the first stage (no twiddles: NS = 1) in registers
+      constexpr int RA = ct::radix_of(KM, 0, true), NBA = E / RA;
+#pragma unroll
+      for (int b = 0; b < NBA; ++b) {
+        Butterfly<RA, true, C>::run(&v[b * RA]);
+#pragma unroll
+        for (int r = 0; r < RA; ++r) st_w((p + P * b) * RA + r, v[b * RA + r]);
+      }
     }
     __syncthreads();
     if (tid == 0 && tn < tlimit) {  // the dense buffer has been read: fetch the next block
       fence_proxy_async_smem();
       issue(tn);
     }
-    ct::stages<R, M, E, true, Pol::FUSE ? 2 : 0, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
+    ct::stages<R, M, E, true, HEAD, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
     ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
     // line -> (realization, x, y): line counts stay below 2^32 (N <= 4096, the
     // host bounds the batch), so 32-bit divisions suffice
