@@ -264,6 +264,18 @@ gg_status gg_batch_sync(gg_batch_t *batch);
  * use. Waits for a previous run and drops the captured graph. */
 gg_status gg_batch_set_persistent(gg_batch_t *batch, int on);
 
+/* Fault test of the persistent launch's bounded waits (no paper
+ * counterpart; off unless armed). kind GG_TEST_STALL_COUNT makes the next
+ * gg_batch_run's first y forward work item of the first group skip counting
+ * itself done: every wait on that pass of that realization gives up after
+ * wait_us microseconds (1 <= wait_us <= 1000000), the launch stops early
+ * (its outputs are meaningless) and gg_batch_sync returns GG_ETIMEOUT. The
+ * graph is captured again for that run and again after it; later runs are
+ * normal. Needs the persistent schedule (else GG_EINVAL). GG_TEST_NONE
+ * disarms. No GPU fault, trap or unbounded wait is involved. */
+#define GG_TEST_STALL_COUNT 2
+gg_status gg_batch_test_arm_fault(gg_batch_t *batch, int kind, uint32_t wait_us);
+
 /* Number of groups and total cells of the batch. */
 gg_status gg_batch_info(const gg_batch_t *batch, int *groups, int64_t *cells);
 

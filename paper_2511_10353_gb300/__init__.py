@@ -26,7 +26,7 @@ _LIB_PATH = os.path.join(_HERE, "libgg.so")
 _lib = None
 
 GG_OK, GG_EINVAL, GG_ENOMEM, GG_ECUDA, GG_ETIMEOUT = 0, -1, -2, -3, -4
-GG_TEST_NONE, GG_TEST_SKIP_COPY = 0, 1
+GG_TEST_NONE, GG_TEST_SKIP_COPY, GG_TEST_STALL_COUNT = 0, 1, 2
 GG_F32, GG_F64 = 0, 1
 TF = {"bbks": 0, "eh_nw": 1, "table": 2}
 GG_Q_CORNER = 0x1
@@ -114,6 +114,7 @@ _SIGS = {
     "gg_batch_free": (None, [ctypes.c_void_p]),
     "gg_batch_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "gg_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gg_batch_test_arm_fault": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]),
     "gg_zeldovich_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_smooth": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "gg_cic_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -631,6 +632,12 @@ class Batch:
         chunk: most tiles per work item (a power of two up to 256; default 64)."""
         v = (int(chunk) if chunk else 1) if on else 0
         _check(lib().gg_batch_set_persistent(self._h, v))
+
+    def arm_fault(self, kind="stall_count", wait_us=2000):
+        """Fault test: the next persistent run stalls one pass counter, so its
+        waits give up after wait_us and the next sync raises GG_ETIMEOUT."""
+        k = {"none": GG_TEST_NONE, "stall_count": GG_TEST_STALL_COUNT}[kind]
+        _check(lib().gg_batch_test_arm_fault(self._h, k, int(wait_us)))
 
     def launches(self):
         """Kernels one run launches (kernel nodes of the captured graph)."""

@@ -126,6 +126,10 @@ struct gg_batch {
   // one persistent launch for the whole batch (gg_batch_set_persistent)
   bool persistent = false;
   int persist_chunk = 0;             // most tiles per work item (0: the default)
+  // fault test (gg_batch_test_arm_fault): the next persistent run stalls one
+  // pass counter; the graph is captured again before and after that run
+  int test_stall = 0, test_ran = 0;
+  uint32_t test_wait_us = 0;
   unsigned int *counters = nullptr;  // device: work queue, abort flag, pass counters
   int persist_blocks = 0;
 };
@@ -1239,6 +1243,8 @@ gg_status persist_passes(gg_batch_t *b, cudaStream_t s, uint32_t sig) {
   pp.counters = b->counters;
   pp.err = b->groups[0].plan->err;
   pp.chunk = b->persist_chunk;
+  pp.test_stall = b->test_stall;
+  pp.wait_us = b->test_stall ? b->test_wait_us : 0;
   cudaError_t e;
   int first = 0;
   for (int gi = 0; gi < pp.ngroups; ++gi) {
@@ -1846,6 +1852,13 @@ gg_status gg_batch_run(gg_batch_t *b, const uint64_t *seeds, void *const *psi, v
         else all &= ~(1u << (o * 3 + j));
       }
   sig |= all << 9;
+  if ((b->test_stall || b->test_ran) && b->exec) {  // capture with (or again without) the fault
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  b->test_ran = b->test_stall;
   for (auto &g : b->groups) {
     const int nb = (int)g.members.size();
     for (int k = 0; k < nb; ++k) {
@@ -1898,6 +1911,21 @@ gg_status gg_batch_run(gg_batch_t *b, const uint64_t *seeds, void *const *psi, v
       (e = cudaEventRecord(b->done, b->stream)) != cudaSuccess)
     return cuda_fail(nullptr, e, "cudaGraphLaunch");
   b->ran = true;
+  b->test_stall = 0;
+  return GG_OK;
+}
+
+gg_status gg_batch_test_arm_fault(gg_batch_t *b, int kind, uint32_t wait_us) {
+  if (!b) return fail(nullptr, GG_EINVAL, "batch is NULL");
+  if (kind == GG_TEST_NONE) {
+    b->test_stall = 0;
+    return GG_OK;
+  }
+  if (kind != GG_TEST_STALL_COUNT) return fail(nullptr, GG_EINVAL, "unknown fault kind");
+  if (!b->persistent) return fail(nullptr, GG_EINVAL, "the stall test needs the persistent schedule");
+  if (wait_us < 1 || wait_us > 1000000) return fail(nullptr, GG_EINVAL, "wait_us must be in [1, 1e6]");
+  b->test_stall = 1;
+  b->test_wait_us = wait_us;
   return GG_OK;
 }
 

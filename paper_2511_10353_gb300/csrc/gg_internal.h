@@ -249,6 +249,7 @@ struct PersistPlan {
   int *err;               // device error word (2: a wait gave up)
   uint32_t wait_us;       // limit of every wait (0: two seconds)
   int chunk;              // most tiles per work item (a power of two; 0: 64)
+  int test_stall;         // fault test: the first y forward item never counts itself done
 };
 bool persist_has(int n);
 // Fills the tile shapes and tensor maps and launches on s (capturable).

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(const __grid_constant__
     if (tid == 0) {
       if (!ok) {
         atomicExch(&counters[1], 1u);
-      } else {
+      } else if (!(P.p.test_stall && pass == 1 && gi == 0 && t == 0)) {  // fault test: stall
         __threadfence();
         const int64_t rr = t / P.per_real[pass][gi];
         atomicAdd(&done[(size_t)(P.p.g[gi].first + rr) * kPersistPasses + pass], 1u);

@@ -56,3 +56,31 @@ def test_disarm_and_argument_checks(gg):
     plan.sync()
     assert np.isfinite(out[0].cpu().numpy()).all()
     plan.close()
+
+
+def test_persistent_batch_wait_timeout_and_recovery(gg):
+    """The persistent batched launch: one work item never counts itself done,
+    so every wait on its pass gives up after a few milliseconds; the run
+    stops, gg_batch_sync reports GG_ETIMEOUT, and the next run (the graph
+    captured again without the fault) equals the normal result."""
+    specs = [dict(n=64, box=64.0, cosmo=BBKS, z_init=50.0),
+             dict(n=128, box=128.0, cosmo=BBKS, z_init=50.0)]
+    b = gg.Batch(specs)
+    b.set_persistent(True)
+    ref = b.empty_outputs()
+    b.run([1, 2], ref)
+    b.sync()
+    ref = {k: [[t.clone() if t is not None else None for t in r] for r in v] for k, v in ref.items()}
+    out = b.empty_outputs()
+    b.arm_fault("stall_count", wait_us=3000)
+    b.run([1, 2], out)
+    with pytest.raises(gg.GGError) as ex:
+        b.sync()
+    assert ex.value.status == gg.GG_ETIMEOUT
+    b.run([1, 2], out)
+    b.sync()
+    for k in ("pos", "vel"):
+        for i in range(2):
+            for j in range(3):
+                assert torch.equal(out[k][i][j], ref[k][i][j]), (k, i, j)
+    b.close()
