@@ -224,6 +224,20 @@ __device__ __forceinline__ int k_of(int p, int b) {
   }
 }
 
+// A twiddle table: in shared memory (SM: the strided passes of the
+// large-radix schedules copy it there) or in global memory, read through the
+// non-coherent cache.
+template <typename T, bool SM> struct Tw {
+  const T *p;
+  __device__ __forceinline__ T operator[](int i) const {
+    if constexpr (SM) return p[i];
+    else return __ldg(p + i);
+  }
+};
+template <typename T> __device__ __forceinline__ Tw<T, false> tw_global(const void *p) {
+  return Tw<T, false>{reinterpret_cast<const T *>(p)};
+}
+
 // Twiddles of a stage with NS > 1: FP32 radices up to 8 load w^1 per
 // butterfly (before the stage's shared-memory reads, to overlap their
 // latency) and form the other powers by at most three products; FP64, and
@@ -232,15 +246,14 @@ __device__ __forceinline__ int k_of(int p, int b) {
 template <typename R, int RAD> __host__ __device__ constexpr bool powers_from_w1() {
   return sizeof(R) == 4 && (RAD == 2 || RAD == 3 || RAD == 4 || RAD == 8);
 }
-template <typename R, int RAD, bool INV, int TSTEP>
-__device__ __forceinline__ void stage_twiddles(Cx<R> *v, int k, Cx<R> w1,
-                                               const Cx<R> *__restrict__ tw) {
+template <typename R, int RAD, bool INV, int TSTEP, class TwT>
+__device__ __forceinline__ void stage_twiddles(Cx<R> *v, int k, Cx<R> w1, const TwT &tw) {
   if constexpr (powers_from_w1<R, RAD>()) {
     twiddle_powers<RAD, INV>(v, w1);
   } else {
 #pragma unroll
     for (int r = 1; r < RAD; ++r) {
-      const Cx<R> w = ldg_c(tw + k * TSTEP * r);
+      const Cx<R> w = tw[k * TSTEP * r];
       v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
     }
   }
@@ -258,8 +271,8 @@ template <int SY> __device__ __forceinline__ void stage_barrier() {
 // (INV = false) or inverse schedule, for the butterflies j = p + P*b of this
 // thread. ld(n) reads element n of the stage input, st(n, v) writes element n
 // of its output; with a barrier (SY) the stage runs in place in shared memory.
-template <typename R, int N, int E, int SI, bool INV, int SY, class Ld, class St>
-__device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
+template <typename R, int N, int E, int SI, bool INV, int SY, class Ld, class St, class TwT>
+__device__ __forceinline__ void stage(int p, const TwT &tw, const Ld &ld,
                                       const St &st) {
   constexpr int K = skey<R>(N);
   constexpr int RAD = radix_of(K, SI, INV);
@@ -269,7 +282,7 @@ __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const
   Cx<R> w1[NB];
   if constexpr (NS > 1 && powers_from_w1<R, RAD>()) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b) w1[b] = ldg_c(tw + k_of<NS, P, NB>(p, b) * TSTEP);
+    for (int b = 0; b < NB; ++b) w1[b] = tw[k_of<NS, P, NB>(p, b) * TSTEP];
   }
   Cx<R> v[E];
 #pragma unroll
@@ -295,8 +308,8 @@ __device__ __forceinline__ void stage(int p, const Cx<R> *__restrict__ tw, const
 
 // Stages FIRST .. LAST-1 in place in shared memory, barrier SY.
 template <typename R, int N, int E, bool INV, int FIRST, int LAST, int SY = kSyncCta, class Ld,
-          class St>
-__device__ __forceinline__ void stages(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
+          class St, class TwT>
+__device__ __forceinline__ void stages(int p, const TwT &tw, const Ld &ld,
                                        const St &st) {
   if constexpr (FIRST < LAST) {
     stage<R, N, E, FIRST, INV, SY>(p, tw, ld, st);
@@ -308,8 +321,8 @@ __device__ __forceinline__ void stages(int p, const Cx<R> *__restrict__ tw, cons
 // A and writes B, the next reads B and writes A, ...): one CTA barrier per
 // stage instead of two. The caller leaves B free; an even count ends in A.
 template <typename R, int N, int E, bool INV, int FIRST, int LAST, class LdA, class StA, class LdB,
-          class StB>
-__device__ __forceinline__ void stages_pingpong(int p, const Cx<R> *__restrict__ tw, const LdA &lda,
+          class StB, class TwT>
+__device__ __forceinline__ void stages_pingpong(int p, const TwT &tw, const LdA &lda,
                                                 const StA &sta, const LdB &ldb, const StB &stb) {
   if constexpr (FIRST < LAST) {
     stage<R, N, E, FIRST, INV, kSyncNone>(p, tw, lda, stb);
@@ -320,8 +333,8 @@ __device__ __forceinline__ void stages_pingpong(int p, const Cx<R> *__restrict__
 
 // The last stage of a schedule, outputs kept in registers: on return v holds
 // element j + r*N/RAD at v[b*RAD + r] (j = p + P*b).
-template <typename R, int N, int E, bool INV, class Ld>
-__device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__ tw, const Ld &ld,
+template <typename R, int N, int E, bool INV, class Ld, class TwT>
+__device__ __forceinline__ void last_stage_regs(int p, const TwT &tw, const Ld &ld,
                                                 Cx<R> *v) {
   constexpr int K = skey<R>(N);
   constexpr int S = nstages(K);
@@ -333,7 +346,7 @@ __device__ __forceinline__ void last_stage_regs(int p, const Cx<R> *__restrict__
   Cx<R> w1[NB];
   if constexpr (NS > 1 && powers_from_w1<R, RAD>()) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b) w1[b] = ldg_c(tw + k_of<NS, P, NB>(p, b) * TSTEP);
+    for (int b = 0; b < NB; ++b) w1[b] = tw[k_of<NS, P, NB>(p, b) * TSTEP];
   }
 #pragma unroll
   for (int b = 0; b < NB; ++b)
@@ -360,14 +373,14 @@ template <typename R, int N, int E> __host__ __device__ constexpr bool fuse_pair
 }
 
 // Twiddles w^(k r), r = 1 .. RAD-1, on one butterfly's inputs; kt = k*TSTEP.
-template <typename R, int RAD, bool INV>
-__device__ __forceinline__ void stage_twiddle(Cx<R> *v, const Cx<R> *__restrict__ tw, int kt) {
+template <typename R, int RAD, bool INV, class TwT>
+__device__ __forceinline__ void stage_twiddle(Cx<R> *v, const TwT &tw, int kt) {
   if constexpr (sizeof(R) == 4) {
-    twiddle_powers<RAD, INV>(v, ldg_c(tw + kt));
+    twiddle_powers<RAD, INV>(v, tw[kt]);
   } else {
 #pragma unroll
     for (int r = 1; r < RAD; ++r) {
-      const Cx<R> w = ldg_c(tw + kt * r);
+      const Cx<R> w = tw[kt * r];
       v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
     }
   }
@@ -377,8 +390,8 @@ __device__ __forceinline__ void stage_twiddle(Cx<R> *v, const Cx<R> *__restrict_
 // the contract of last_stage_regs. Stage A's butterflies of this thread are
 // j = p + P*b, b = g + G*q (k = p + P*g, q < RB); their outputs are the inputs
 // of stage B's butterflies j' = p + P*(g + G*r), input q.
-template <typename R, int N, int E, class Ld>
-__device__ __forceinline__ void last_two_stages_regs(int p, const Cx<R> *__restrict__ tw,
+template <typename R, int N, int E, class Ld, class TwT>
+__device__ __forceinline__ void last_two_stages_regs(int p, const TwT &tw,
                                                      const Ld &ld, Cx<R> *v) {
   constexpr int K = skey<R>(N);
   constexpr int S = nstages(K);
@@ -391,7 +404,7 @@ __device__ __forceinline__ void last_two_stages_regs(int p, const Cx<R> *__restr
   Cx<R> w1[NBA];
   if constexpr (sizeof(R) == 4) {
 #pragma unroll
-    for (int b = 0; b < NBA; ++b) w1[b] = ldg_c(tw + k_of<NSA, P, NBA>(p, b) * TSA);
+    for (int b = 0; b < NBA; ++b) w1[b] = tw[k_of<NSA, P, NBA>(p, b) * TSA];
   }
   Cx<R> a[E];
 #pragma unroll
@@ -426,8 +439,8 @@ __device__ __forceinline__ void last_two_stages_regs(int p, const Cx<R> *__restr
 // butterfly (g, r) = j' = p*RA + P*RA*g + r, whose k = r is known at compile
 // time. On return v[(g*RA + r)*RB + s] holds stage B's output s of butterfly
 // (g, r); inverse_head_store writes them.
-template <typename R, int N, int E>
-__device__ __forceinline__ void inverse_head_regs(const Cx<R> *__restrict__ tw, Cx<R> *v) {
+template <typename R, int N, int E, class TwT>
+__device__ __forceinline__ void inverse_head_regs(const TwT &tw, Cx<R> *v) {
   constexpr int RA = radix_of(skey<R>(N), 0, true), RB = radix_of(skey<R>(N), 1, true);
   constexpr int P = N / E, G = E / (RA * RB), NBA = E / RA;
   constexpr int TSB = N / (RA * RB);
@@ -522,6 +535,10 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr bool SPILL = (BIG && V == 1) || REG_NEED > REG_BUDGET;
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
   static_assert(V != kPersistV || (THREADS == 256 && (N / 2) % B == 0), "persistent tile");
+  // the large radices read their stage twiddles from a shared-memory copy
+  // where it fits beside the tiles and the largest filter table
+  static constexpr bool TW_SMEM = BIG && sizeof(R) == 4 && V != kPersistV &&
+                                  SMEM_EST + N * CB + 4 * kInterpExact + 16 * kMaxInterpCells(N) <= 227 * 1024;
 };
 
 // z passes: lines per tile, variant 0 ~256 threads (sized so that two dense

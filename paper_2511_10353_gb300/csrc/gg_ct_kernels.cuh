@@ -59,11 +59,19 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
   const int tid = threadIdx.x;
   const int64_t per_real = (int64_t)N * INNER;
   const int64_t ntiles = per_real * (a.nbatch > 0 ? a.nbatch : 1);
-  const C *tw = reinterpret_cast<const C *>(a.tw);
   const R *table = reinterpret_cast<const R *>(a.table);
   static_assert(FILT != kFiltInterp || sizeof(R) == 4, "interpolated filter: FP32");
   const bool pre = FILT == kFiltArgs ? a.pre != 0 : FILT == kFiltInterp;
   const bool interp = FILT == kFiltArgs ? sizeof(R) == 4 && a.pre && a.interp : FILT == kFiltInterp;
+  // large radices: the N twiddles in shared memory (15-31 loads a butterfly),
+  // after the tiles and the filter table
+  constexpr bool TW_SMEM = ct::AxisPolicy<R, N, V>::TW_SMEM;
+  C *tw_s = bufs + 2 * TILE_STRIDE + (interp ? (kInterpExact + 4 * kMaxInterpCells(N)) / 2 : 0);
+  if constexpr (TW_SMEM) {
+    const C *src = reinterpret_cast<const C *>(a.tw);
+    for (int i = tid; i < N; i += blockDim.x) tw_s[i] = src[i];
+  }
+  const ct::Tw<C, TW_SMEM> tw{TW_SMEM ? tw_s : reinterpret_cast<const C *>(a.tw)};
   if (interp) {
     const float *src = reinterpret_cast<const float *>(a.interp);
     for (int i = tid; i < kInterpExact; i += blockDim.x) f_exact[i] = src[i];
@@ -318,7 +326,7 @@ __device__ __forceinline__ bool zinv_body(const ZInvArgs &a, int64_t t0, int64_t
   C *work = dense + DENSE_STRIDE;
   const int tid = threadIdx.x;
   const int64_t ntiles = a.nlines / L;
-  const C *tw_half = reinterpret_cast<const C *>(a.tw_half);
+  const ct::Tw<C, false> tw_half{reinterpret_cast<const C *>(a.tw_half)};
   const C *twf = reinterpret_cast<const C *>(a.tw_full);
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -473,7 +481,7 @@ __device__ __forceinline__ void zfwd_body(const ZFwdArgs &a, int64_t t0, int64_t
   C *work = reinterpret_cast<C *>(smem_raw);
   const int tid = threadIdx.x;
   const int64_t ntiles = a.nlines / L;
-  const C *tw_half = reinterpret_cast<const C *>(a.tw_half);
+  const ct::Tw<C, false> tw_half{reinterpret_cast<const C *>(a.tw_half)};
   const C *twf = reinterpret_cast<const C *>(a.tw_full);
   if (tlimit > ntiles) tlimit = ntiles;
   for (int64_t t = t0; t < tlimit; t += tstep) {
@@ -555,8 +563,11 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const size_t tile = ((size_t)N * Pol::B * 2 * sizeof(R) + 127) & ~(size_t)127;
   const bool interp = sizeof(R) == 4 && a.pre && a.interp;
-  const size_t smem = 128 + 2 * tile +
-                      (interp ? kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16 : 0);
+  const size_t filt = interp ? (Pol::TW_SMEM ? kInterpExact * sizeof(float) + (size_t)kMaxInterpCells(N) * 16
+                                              : kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16)
+                             : 0;
+  const size_t smem = 128 + 2 * tile + filt + (Pol::TW_SMEM ? (size_t)N * 2 * sizeof(R) : 0);
+  if (interp && a.interp_cells > kMaxInterpCells(N)) return cudaErrorInvalidValue;
   auto kern = k_axis_ct<R, N, V, MODE, CUT, FILT>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);

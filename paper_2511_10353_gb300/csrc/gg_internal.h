@@ -13,6 +13,8 @@ namespace gg {
 
 constexpr int kMaxStages = 16;
 constexpr int kInterpExact = 1024;  // m2 below this: exact table values in shared memory
+// most unit cells in m = sqrt(m2) of the interpolated filter for grids of n points
+__host__ __device__ constexpr int kMaxInterpCells(int n) { return (int)(1.7320508075688772 * (n / 2)) + 3; }
 
 // Radix schedule of one complex transform of length `len` done inside a CTA
 // (Stockham autosort, decimation in time). Stage s combines radix[s] partial
