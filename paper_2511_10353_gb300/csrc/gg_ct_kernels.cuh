@@ -498,7 +498,10 @@ __device__ __forceinline__ void zfwd_body(const ZFwdArgs &a, int64_t t0, int64_t
       for (int i = 0; i < E / 2; ++i) {
         const int q = p + P * i;
         R w[4];
-        gauss4(noise_words(seed, g0 + q), w);
+        if constexpr ((int64_t)N * N * N / 4 <= 0xFFFFFFFFll)  // group indices fit 32 bits
+          gauss4(noise_words32(seed, (uint32_t)(g0 + q)), w);
+        else
+          gauss4(noise_words(seed, g0 + q), w);
         work[zpad<LD, PAD>(l, 2 * q)] = C{w[0], w[1]};
         work[zpad<LD, PAD>(l, 2 * q + 1)] = C{w[2], w[3]};
       }

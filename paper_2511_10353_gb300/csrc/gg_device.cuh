@@ -65,6 +65,12 @@ __device__ __forceinline__ uint4 noise_words(uint64_t seed, uint64_t group) {
   return philox4x32_10((uint32_t)group, (uint32_t)(group >> 32), 0u, 0u, (uint32_t)seed,
                        (uint32_t)(seed >> 32));
 }
+// The same for a group index below 2^32 (every group of a grid of N <= 2048
+// points per axis): the counter's high word is a compile-time zero, which
+// removes a wide multiply from each of the first two rounds. Same words.
+__device__ __forceinline__ uint4 noise_words32(uint64_t seed, uint32_t group) {
+  return philox4x32_10(group, 0u, 0u, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
 
 // Two-output Box-Muller (Box & Muller 1958) on one word pair (r_a, r_b):
 // u_a = (r_a + 1) 2^-32 in (0, 1], u_b = r_b 2^-32; rho = sqrt(-2 ln u_a);
@@ -79,9 +85,11 @@ __device__ __forceinline__ uint4 noise_words(uint64_t seed, uint64_t group) {
 //   (absolute error below 2^-22.6 on [1/2, 2], two ulp elsewhere) times ln 2;
 // * rho = a rsqrt(a), a = -2 ln u_a (0 when u_a = 1);
 // * the angle 2 pi u_b is reduced exactly in integers to the nearest
-//   quarter turn q and a remainder x in [-pi/4, pi/4), sin x and cos x are
-//   their Taylor series to x^9 and x^10 (truncation below 2e-9), and the
-//   quarter turn is applied by swaps and signs.
+//   quarter turn q and a remainder x in [-pi/4, pi/4), sin x / x and cos x
+//   are polynomials in x^2 of degrees 3 and 4 fitted by weighted least
+//   squares on 20001 Chebyshev points of [-pi/4, pi/4] (relative error of
+//   sin below 4e-9, absolute error of cos below 6e-11, both far below an
+//   FP32 ulp), and the quarter turn is applied by swaps and signs.
 // Against the FP64 form: relative L2 about 1e-7, largest difference about
 // 1e-6 (the pair's cos/sin rounding, and near u_a = 1 the FP32 rounding of
 // a tiny rho).
@@ -98,14 +106,12 @@ __device__ __forceinline__ void sincos_turn32(uint32_t rb, float &s, float &c) {
   const int32_t t = (int32_t)(rb - (q << 30));   // remainder, |t| <= 2^29 (an eighth)
   const float x = (float)t * (6.28318530717958648f * 0x1p-32f);
   const float x2 = x * x;
-  float sp = fmaf(x2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
-  sp = fmaf(x2, sp, 8.33333333e-3f);                      // 1/5!
-  sp = fmaf(x2, sp, -1.66666667e-1f);                     // -1/3!
+  float sp = fmaf(x2, -1.9513928466e-4f, 8.3321482266e-3f);
+  sp = fmaf(x2, sp, -1.6666654339e-1f);
   const float sn = fmaf(x * x2, sp, x);
-  float cp = fmaf(x2, -2.75573192e-7f, 2.48015873e-5f);   // -1/10!, 1/8!
-  cp = fmaf(x2, cp, -1.38888889e-3f);                     // -1/6!
-  cp = fmaf(x2, cp, 4.16666667e-2f);                      // 1/4!
-  cp = fmaf(x2, cp, -0.5f);
+  float cp = fmaf(x2, 2.4389199288e-5f, -1.3886747959e-3f);
+  cp = fmaf(x2, cp, 4.1666622701e-2f);
+  cp = fmaf(x2, cp, -4.9999999718e-1f);
   const float cs = fmaf(x2, cp, 1.0f);
   // sin(x + q pi/2), cos(x + q pi/2)
   const float a = (q & 1) ? cs : sn, b = (q & 1) ? sn : cs;
