@@ -23,6 +23,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "gg.h"
 #include "gg_cosmo.h"
@@ -378,12 +379,15 @@ const char *const kKindNames[kNumKinds] = {"z_forward_noise", "y_forward",
                                            "y_inverse_yz",    "z_inverse_epilogue",
                                            "noise"};
 
-// Records a start event before a launch and an end event after it when the
-// plan's profiling is on; `bytes` is the launch's algorithmic HBM traffic.
+// An NVTX range named after the pass around every launch (visible to
+// profilers and tracers; a no-op without one), and, when the plan's
+// profiling is on, a start event before the launch and an end event after
+// it; `bytes` is the launch's algorithmic HBM traffic.
 struct ProfScope {
   gg_plan_t *plan;
   size_t slot = (size_t)-1;
   ProfScope(gg_plan_t *p, int kind, double bytes) : plan(p) {
+    nvtxRangePushA(kKindNames[kind]);
     if (!plan->prof_on) return;
     if (plan->prof_used == plan->prof.size()) {
       gg_plan::ProfRec r{kind, nullptr, nullptr};
@@ -397,6 +401,7 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (slot != (size_t)-1) cudaEventRecord(plan->prof[slot].b, plan->stream);
+    nvtxRangePop();
   }
 };
 
