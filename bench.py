@@ -77,6 +77,9 @@ def parse():
                     help="skip the 1536^3 leg of the default run")
     ap.add_argument("--variants", default=None,
                     help="comma list of 6 tile variants instead of autotuning (profiling runs)")
+    ap.add_argument("--layout", choices=["auto", "plain", "chunked"], default="auto",
+                    help="spectrum layout between the y passes (auto: the autotuner's choice; "
+                         "with --variants, plain unless given)")
     return ap.parse_args()
 
 
@@ -467,7 +470,8 @@ def run_features(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def time_plain(gg, w, steps, warmup, variants_arg, world, barrier, gpu_id, allreduce_max):
+def time_plain(gg, w, steps, warmup, variants_arg, world, barrier, gpu_id, allreduce_max,
+               layout="auto"):
     """Plan, autotune, warm-up, then `steps` timed steps of noise -> pos + vel
     (CUDA events on the plan's stream, per-kernel events on the same stream,
     clocks sampled meanwhile). Returns (result dict, plan, variants)."""
@@ -486,6 +490,8 @@ def time_plain(gg, w, steps, warmup, variants_arg, world, barrier, gpu_id, allre
         variants = plan.variants()
     else:
         variants = plan.autotune(3)  # tile variants per pass, timed on this plan's buffers
+    if layout != "auto":
+        plan.set_layout(layout == "chunked")
     t_tune = time.perf_counter() - t_tune
     for i in range(max(3, warmup)):
         plan.zeldovich(seed=1 + i, out=out)
@@ -534,7 +540,8 @@ def time_plain(gg, w, steps, warmup, variants_arg, world, barrier, gpu_id, allre
     step_bytes = sum(v["bytes"] * v["launches"] for v in prof.values()) / steps
     path_gbs = step_bytes / (ms / steps * 1e-3) / 1e9
     res = {"value": value, "ms_per_step": ms / steps, "steps": steps,
-           "config": dict(config_of(w), tile_variants=variants, autotune_s=round(t_tune, 3)),
+           "config": dict(config_of(w), tile_variants=variants, autotune_s=round(t_tune, 3),
+                          spectrum_layout="chunk-major" if plan.layout() else "plain"),
            "roofline": roofline,
            "path": {"algorithmic_bytes_per_cell": step_bytes / cells, "GB_s": path_gbs,
                     "frac_of_peak": path_gbs / peak},
@@ -662,7 +669,8 @@ def main():
     n = w["n"]
     cells = n ** 3
     res, plan, variants = time_plain(gg, w, args.steps, args.warmup, args.variants, world,
-                                     barrier, gpu_id, allreduce_max)
+                                     barrier, gpu_id, allreduce_max, args.layout)
+    chunked = res["config"]["spectrum_layout"] == "chunk-major"
     value = res["value"]
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
@@ -685,6 +693,7 @@ def main():
         if plan is None:
             plan = gg.Plan(n, w["box"], w["cosmo"], w["z_init"], w["prec"])
             plan.set_variants(variants)
+            plan.set_layout(chunked)
         hn = torch.randn(shape, dtype=dt).pin_memory()
         hout = {"psi": [None] * 3,
                 "pos": [torch.empty(shape, dtype=dt, pin_memory=True) for _ in range(3)],

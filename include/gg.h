@@ -212,6 +212,18 @@ gg_status gg_plan_variants(const gg_plan_t *plan, int32_t out[6]);
  * are rejected). */
 gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]);
 
+/* Layout of the spectrum between the y forward and the y inverse passes of
+ * a three-component run (pos and/or vel of all components, no psi output,
+ * no Sec. 2.4 cut): 0 plain [x][y][k_z]; 1 chunk-major [k_z chunk][x][y]
+ * [tile width], in which a tile of the x pass spans a few hundred kilobytes
+ * per chunk instead of one memory page per row. Results are bit-identical
+ * (same arithmetic in the same order). The chunk-major layout needs the four
+ * strided passes' variants to share a tile width; otherwise the plain one
+ * runs. gg_autotune chooses between them; gg_plan_layout reports the layout
+ * the next run takes (1 only where the chunk-major one applies). */
+gg_status gg_plan_set_layout(gg_plan_t *plan, int32_t chunked);
+gg_status gg_plan_layout(const gg_plan_t *plan, int32_t *out);
+
 /* ---------------------------------------------------------------- batched form
  * Many independent realizations (each its own gg_params; seeds given per run)
  * in one set of launches. Realizations with identical parameters form a

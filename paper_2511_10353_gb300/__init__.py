@@ -103,6 +103,8 @@ _SIGS = {
     "gg_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gg_plan_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gg_plan_set_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gg_plan_set_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "gg_plan_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "gg_batch_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
     "gg_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -537,6 +539,17 @@ class Plan:
         """Force the tile variant per pass (6 ints in 0..2)."""
         arr = (ctypes.c_int32 * 6)(*[int(x) for x in v])
         _check(lib().gg_plan_set_variants(self._h, arr), self._h)
+
+    def set_layout(self, chunked):
+        """Spectrum layout between the y passes of a three-component run:
+        False plain, True chunk-major (bit-identical results)."""
+        _check(lib().gg_plan_set_layout(self._h, 1 if chunked else 0), self._h)
+
+    def layout(self):
+        """True if the next three-component run keeps the spectrum chunk-major."""
+        out = ctypes.c_int32(0)
+        _check(lib().gg_plan_layout(self._h, ctypes.byref(out)), self._h)
+        return bool(out.value)
 
     def set_profiling(self, on=True):
         """Bracket every launch with CUDA events on the plan's stream."""

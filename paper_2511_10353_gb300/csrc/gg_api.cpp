@@ -68,6 +68,7 @@ struct gg_plan {
   // 0 z forward, 1 y forward, 2 x fused, 3 y inverse (x branch),
   // 4 y inverse (y/z branches), 5 z inverse
   int variant[6] = {0, 0, 0, 0, 0, 0};
+  int chunked = 0;  // 1: the three-component chain keeps the spectrum chunk-major
   // fault test (gg_test_arm_fault): the next y forward pass issues no copies
   int test_skip_copy = 0;
   uint32_t test_wait_us = 0;
@@ -443,7 +444,8 @@ gg_status launch_axis_timed(gg_plan_t *plan, const gg::AxisArgs &c, int kind, co
 
 // z forward (noise or caller noise) and y forward into plan->work.
 template <typename R>
-gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
+gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise, void *chunked_dst = nullptr,
+                     int chunk_b = 0) {
   const int n = (int)plan->p.n;
   gg::ZFwdArgs z{};
   z.noise = noise;
@@ -467,9 +469,13 @@ gg_status forward_zy(gg_plan_t *plan, uint64_t seed, const void *noise) {
   c.fwd = 1;
   c.inv = 0;
   c.nout = 1;
-  c.dst[0] = plan->work;
+  c.dst[0] = chunked_dst ? chunked_dst : plan->work;
   c.mul[0] = gg::kMulNone;
   c.variant = plan->variant[1];
+  if (chunked_dst) {
+    c.cols = chunk_b;
+    c.chunked_out = 1;
+  }
   if (plan->test_skip_copy) {  // armed fault test: this launch only
     c.test_skip_copy = 1;
     c.wait_us = plan->test_wait_us;
@@ -529,6 +535,81 @@ gg_status ensure_grid(gg_plan_t *plan, void **buf) {
     return fail(plan, GG_ENOMEM, "cudaMalloc of a component workspace failed");
   }
   return GG_OK;
+}
+
+// The tile width shared by the four strided passes' variants (the width of
+// a chunk-major spectrum's chunks), 0 if they differ or N has no
+// size-specialised kernels.
+template <typename R>
+int chunk_cols(gg_plan_t *plan) {
+  const int n = (int)plan->p.n;
+  if (!gg::spec_has<R>(n) || plan->merge_qmin > 0) return 0;
+  const int b = gg::spec_axis_cols<R>(n, plan->variant[1]);
+  for (int i = 2; i <= 4; ++i)
+    if (gg::spec_axis_cols<R>(n, plan->variant[i]) != b) return 0;
+  return b;
+}
+
+// Positions and velocities of all three components with the spectrum
+// chunk-major between the y forward and the y inverse passes ([k_z chunk][x]
+// [y][cols]): a tile of the x pass, and the concurrent tiles around it, then
+// span a few hundred kilobytes of each chunk instead of one memory page per
+// row. Same arithmetic as the plain chain, in the same order; only the
+// buffers differ:
+//   y forward  work -> work3 (chunk-major)
+//   x fused    work3 -> A: work3 (in place), B: work2 (both chunk-major)
+//   y inverse  work3 -> work (plain); z inverse x from work
+//   y inverse  work2 -> work (i m_y), work3; z inverses y, z
+template <typename R>
+gg_status run_zeldovich_chunked(gg_plan_t *plan, uint64_t seed, const void *noise,
+                                void *const pos[3], void *const vel[3]) {
+  const int b = chunk_cols<R>(plan);
+  gg_status st = forward_zy<R>(plan, seed, noise, plan->work3, b);
+  if (st != GG_OK) return st;
+  gg::AxisArgs x = axis_args<R>(plan, 0, plan->work3);
+  x.cols = b;
+  x.fwd = 1;
+  x.inv = 1;
+  x.pre = 1;
+  x.table = plan->tab.u_phi;
+  x.interp = plan->tab.interp_u;
+  x.interp_cells = plan->tab.interp_cells;
+  x.nout = 2;
+  x.dst[0] = plan->work3;
+  x.mul[0] = gg::kMulIm;
+  x.dst[1] = plan->work2;
+  x.mul[1] = gg::kMulNone;
+  x.chunked_in = 1;
+  x.chunked_out = 1;
+  x.variant = plan->variant[2];
+  if ((st = launch_axis_timed<R>(plan, x, kXFused, "x fused pass")) != GG_OK) return st;
+  gg::AxisArgs y = axis_args<R>(plan, 1, plan->work3);
+  y.cols = b;
+  y.inv = 1;
+  y.nout = 1;
+  y.dst[0] = plan->work;
+  y.mul[0] = gg::kMulNone;
+  y.chunked_in = 1;
+  y.variant = plan->variant[3];
+  if ((st = launch_axis_timed<R>(plan, y, kYInvX, "y inverse pass (x branch)")) != GG_OK) return st;
+  auto out = [&](void *const *a, int j) { return a ? a[j] : nullptr; };
+  if ((st = zinv_pass<R>(plan, 0, plan->work, nullptr, out(pos, 0), out(vel, 0), false)) != GG_OK)
+    return st;
+  gg::AxisArgs y2 = axis_args<R>(plan, 1, plan->work2);
+  y2.cols = b;
+  y2.inv = 1;
+  y2.nout = 2;
+  y2.dst[0] = plan->work;
+  y2.mul[0] = gg::kMulIm;
+  y2.dst[1] = plan->work3;
+  y2.mul[1] = gg::kMulNone;
+  y2.chunked_in = 1;
+  y2.variant = plan->variant[4];
+  if ((st = launch_axis_timed<R>(plan, y2, kYInvYZ, "y inverse pass (y/z branches)")) != GG_OK)
+    return st;
+  if ((st = zinv_pass<R>(plan, 1, plan->work, nullptr, out(pos, 1), out(vel, 1), false)) != GG_OK)
+    return st;
+  return zinv_pass<R>(plan, 2, plan->work3, nullptr, out(pos, 2), out(vel, 2), true);
 }
 
 // Everything up to the inverse z passes. On return src[j] holds, for each
@@ -610,6 +691,13 @@ gg_status run_zeldovich(gg_plan_t *plan, uint64_t seed, const void *noise, void 
   for (int j = 0; j < 3; ++j)
     want[j] = (psi && psi[j]) || (pos && pos[j]) || (vel && vel[j]);
   if (!want[0] && !want[1] && !want[2]) return GG_OK;
+  const bool any_psi = psi && (psi[0] || psi[1] || psi[2]);
+  if (plan->chunked && !any_psi && want[0] && want[1] && want[2] && chunk_cols<R>(plan) > 0) {
+    gg_status st = GG_OK;
+    if ((st = ensure_grid(plan, &plan->work2)) != GG_OK) return st;
+    if ((st = ensure_grid(plan, &plan->work3)) != GG_OK) return st;
+    return run_zeldovich_chunked<R>(plan, seed, noise, pos, vel);
+  }
   void *src[3];
   gg_status st = spectral_passes<R>(plan, seed, noise, want, psi, src);
   if (st != GG_OK) return st;
@@ -781,6 +869,7 @@ gg_status autotune(gg_plan_t *plan, int reps) {
     best_v[i] = 0;
   }
   const bool prof_was = plan->prof_on;
+  plan->chunked = 0;  // the variants are timed in the plain layout
   void *vel[3] = {tmp, tmp, tmp};
   const int vmax = std::max(gg::kSpecZVariants, gg::kSpecAxisVariants);
   for (int v = 0; v < vmax; ++v) {
@@ -812,9 +901,37 @@ gg_status autotune(gg_plan_t *plan, int reps) {
     plan->prof_ms[k] = 0;
     plan->prof_launches[k] = 0;
   }
+  for (int i = 0; i < 6; ++i) plan->variant[i] = best_v[i];
+  // the layout between the y passes: chunk-major where the chosen strided
+  // variants share a tile width and the whole three-component step is faster
+  plan->chunked = 0;
+  if (st == GG_OK && chunk_cols<R>(plan) > 0) {
+    void *pos[3] = {tmp, tmp, tmp};  // same traffic for both layouts
+    double t[2] = {0, 0};
+    const bool prof_keep = plan->prof_on;
+    plan->prof_on = false;
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    for (int layout = 0; layout < 2 && st == GG_OK; ++layout) {
+      plan->chunked = layout;
+      if ((st = run_zeldovich<R>(plan, 1, nullptr, nullptr, pos, vel)) != GG_OK) break;  // warm
+      cudaEventRecord(ev[0], plan->stream);
+      for (int r = 0; r < reps && st == GG_OK; ++r)
+        st = run_zeldovich<R>(plan, 1 + r, nullptr, nullptr, pos, vel);
+      cudaEventRecord(ev[1], plan->stream);
+      float ms = 0;
+      if (st == GG_OK && cudaEventSynchronize(ev[1]) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+        t[layout] = ms;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    plan->prof_on = prof_keep;
+    plan->chunked = (st == GG_OK && t[1] > 0 && t[1] < t[0]) ? 1 : 0;
+  }
   cudaStreamSynchronize(plan->stream);
   cudaFree(tmp);
-  for (int i = 0; i < 6; ++i) plan->variant[i] = best_v[i];
   return st;
 }
 
@@ -1726,6 +1843,19 @@ gg_status gg_plan_set_variants(gg_plan_t *plan, const int32_t v[6]) {
     if (v[i] < 0 || v[i] >= nv) return fail(plan, GG_EINVAL, "variant out of range");
   }
   for (int i = 0; i < 6; ++i) plan->variant[i] = v[i];
+  return GG_OK;
+}
+
+gg_status gg_plan_set_layout(gg_plan_t *plan, int32_t chunked) {
+  if (!plan || (chunked != 0 && chunked != 1)) return fail(plan, GG_EINVAL, "plan NULL or layout not 0/1");
+  plan->chunked = chunked;
+  return GG_OK;
+}
+
+gg_status gg_plan_layout(const gg_plan_t *plan, int32_t *out) {
+  if (!plan || !out) return fail(nullptr, GG_EINVAL, "plan or out is NULL");
+  *out = plan->chunked && (plan->real_bytes == 8 ? chunk_cols<double>(const_cast<gg_plan_t *>(plan))
+                                                 : chunk_cols<float>(const_cast<gg_plan_t *>(plan))) > 0;
   return GG_OK;
 }
 

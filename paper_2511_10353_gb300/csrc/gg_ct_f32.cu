@@ -8,5 +8,6 @@ namespace gg {
 using TableF32 = CtTable<float, 64, 128, 192, 256, 384, 512, 1536>;
 template <> bool spec_has<float>(int n) { return TableF32::has(n); }
 template <> cudaError_t spec_axis<float>(const AxisArgs &a, cudaStream_t s) { return TableF32::axis(a, s); }
+template <> int spec_axis_cols<float>(int n, int v) { return TableF32::cols(n, v); }
 
 }  // namespace gg

@@ -84,18 +84,40 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int64_t t, int sb) {
-    const int rr = (int)(t / per_real);
+  // tile t -> (realization, outer index, chunk of columns). The x pass walks
+  // a chunk-major source chunk-outer, so that concurrent tiles share pages;
+  // the y passes keep the outer-major order, in which concurrent tiles write
+  // adjacent columns of the plain layout.
+  const bool cin = a.chunked_in != 0;
+  const bool chunk_outer = cin && a.axis == 0;
+  auto decode = [&](int64_t t, int64_t &rr, int64_t &outer, int &chunk) {
+    rr = t / per_real;
     const int64_t tt = t - rr * per_real;
-    const int64_t outer = tt / INNER;
-    const int chunk = (int)(tt - outer * INNER);
+    if (chunk_outer) {
+      chunk = (int)(tt / N);
+      outer = tt - (int64_t)chunk * N;
+    } else {
+      outer = tt / INNER;
+      chunk = (int)(tt - outer * INNER);
+    }
+  };
+  auto issue = [&](int64_t t, int sb) {
+    int64_t rr, outer;
+    int chunk;
+    decode(t, rr, outer, chunk);
     C *dst = bufs + sb * TILE_STRIDE;
     if (a.test_skip_copy) return;  // fault test: the wait for this tile runs out
     mbar_arrive_expect_tx(&bars[sb], (uint32_t)(TILE * sizeof(C)));
 #pragma unroll
     for (int i = 0; i < N; i += Pol::ROWS_BOX) {
-      if (a.axis == 1) tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, i, (int)outer, rr);
-      else tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, (int)outer, i, rr);
+      if (cin) {
+        if (a.axis == 1) tma_load_5d(dst + i * B, &map, &bars[sb], 0, i, (int)outer, chunk, (int)rr);
+        else tma_load_5d(dst + i * B, &map, &bars[sb], 0, (int)outer, i, chunk, (int)rr);
+      } else if (a.axis == 1) {
+        tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, i, (int)outer, (int)rr);
+      } else {
+        tma_load_4d(dst + i * B, &map, &bars[sb], chunk * B * 2, (int)outer, i, (int)rr);
+      }
     }
   };
   // late: one input buffer (0) and one work buffer (1); the copy of the next
@@ -114,14 +136,18 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     }
     int c = tid & (B - 1), p = tid / B;
     asm volatile("" : "+r"(c), "+r"(p));
-    const int64_t rr = t / per_real;
-    const int64_t tt = t - rr * per_real;
-    const int64_t outer = tt / INNER;
-    const int chunk = (int)(tt - outer * INNER);
+    int64_t rr, outer;
+    int chunk;
+    decode(t, rr, outer, chunk);
     const int kz = chunk * B + c;
     C *buf = bufs + sb * TILE_STRIDE;
     C *wb = late ? bufs + TILE_STRIDE : buf;  // the inverse work buffer
-    const int64_t gbase = rr * a.batch_stride + outer * a.outer_stride + kz;
+    // outputs: the plain layout, or chunk-major (rows B apart along y, N B along x)
+    const int64_t gbase =
+        a.chunked_out ? rr * a.batch_stride + (a.axis == 1 ? ((int64_t)chunk * N + outer) * N * B
+                                                           : ((int64_t)chunk * N * N + outer) * B) + c
+                      : rr * a.batch_stride + outer * a.outer_stride + kz;
+    const int64_t ostride = a.chunked_out ? (a.axis == 1 ? (int64_t)B : (int64_t)N * B) : a.stride;
     const int m_outer = a.axis == 0 ? ct_freq((int)outer, N) : 0;
     const bool nyq_outer = a.axis == 0 && (int)outer == HALF;
     auto tab_index = [&](int n) {
@@ -201,7 +227,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * a.stride] = X[b * RH + r];
+        for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * ostride] = X[b * RH + r];
       __syncthreads();
       continue;
     }
@@ -219,7 +245,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     for (int o = 0; o < a.nout; ++o) {
       asm volatile("" : "+r"(c), "+r"(p));
       C *d = reinterpret_cast<C *>(a.dst[o]) + gbase;
-      auto st_glob = [&](int n, C v) { d[(int64_t)n * a.stride] = v; };
+      auto st_glob = [&](int n, C v) { d[(int64_t)n * ostride] = v; };
       C W[E];
       const bool im = a.mul[o] == kMulIm;
 #pragma unroll
@@ -557,6 +583,7 @@ template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFilt
 cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   using Pol = ct::AxisPolicy<R, N, V>;
   AxisArgs a = in;
+  if ((a.chunked_in || a.chunked_out) && a.cols != Pol::B) return cudaErrorInvalidValue;
   a.cols = Pol::B;
   a.inner_chunks = (N / 2) / Pol::B;
   a.rows_box = Pol::ROWS_BOX;
@@ -607,6 +634,14 @@ constexpr int kZVariants = 4;
 // Run-time dispatch over the specialised sizes and their tile variants.
 template <typename R, int... NS> struct CtTable {
   static bool has(int n) { return ((n == NS) || ...); }
+  template <int N> static int cols_n(int v) {
+    return v == 1 ? ct::AxisPolicy<R, N, 1>::B : (v == 2 ? ct::AxisPolicy<R, N, 2>::B : ct::AxisPolicy<R, N, 0>::B);
+  }
+  static int cols(int n, int v) {
+    int c = 0;
+    ((n == NS ? (c = cols_n<NS>(v), 0) : 0), ...);
+    return c;
+  }
   template <int N, int V> static cudaError_t axis_v(const AxisArgs &a, cudaStream_t s) {
     if (a.fwd && a.inv) {
       if constexpr (sizeof(R) == 4)

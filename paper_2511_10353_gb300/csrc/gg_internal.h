@@ -82,6 +82,11 @@ struct AxisArgs {
   int nbatch;             // realizations in the buffers (<= 0 means 1), outermost
   int64_t batch_stride;   // complex elements between realizations
   int qmin;               // with pre: modes with m2 < qmin get 0 (Eq. 4 top hat; 0: none)
+  // Chunk-major spectra [realization][k_z chunk][x][y][cols] (cols complex
+  // columns per chunk, the codelet's tile width): a tile of either strided
+  // axis then spans few memory pages. chunked_in: src has that layout (tiles
+  // taken chunk-outer); chunked_out: every dst has it.
+  int chunked_in, chunked_out;
   // fault test (gg_test_arm_fault): no tile copy is issued, so every CTA's
   // first wait gives up after wait_us and reports GG_ETIMEOUT; 0 normally
   int test_skip_copy;
@@ -224,6 +229,9 @@ template <typename R> bool spec_has(int n);
 constexpr int kSpecAxisVariants = 3;  // tile variants the autotuner times per strided pass
 constexpr int kSpecZVariants = 4;     // ... per z pass
 template <typename R> cudaError_t spec_axis(const AxisArgs &a, cudaStream_t s);
+// Tile width (complex columns) of the size-specialised strided pass at n in
+// tile variant v (0 when n has no specialised kernels).
+template <typename R> int spec_axis_cols(int n, int v);
 template <typename R> cudaError_t spec_zinv(const ZInvArgs &a, cudaStream_t s);
 template <typename R> cudaError_t spec_zfwd(const ZFwdArgs &a, cudaStream_t s);
 // Persistent batched form (gg_persist.cu): every pass of every realization

@@ -51,7 +51,21 @@ static cudaError_t make_map(CUtensorMap *m, const AxisArgs &a) {
   box[1] = a.axis == 1 ? (cuuint32_t)a.rows_box : 1u;
   box[2] = a.axis == 1 ? 1u : (cuuint32_t)a.rows_box;
   box[3] = 1u;
-  cuuint32_t estr[4] = {1, 1, 1, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (a.chunked_in) {  // [nbatch][N/2 / cols][N (x)][N (y)][cols] complex
+    const cuuint64_t cw = 2 * (cuuint64_t)a.cols;  // reals of one chunk row
+    cuuint64_t d5[5] = {cw, (cuuint64_t)a.n, (cuuint64_t)a.n, half / a.cols, nb};
+    cuuint64_t s5[4] = {cw * sizeof(R), (cuuint64_t)a.n * cw * sizeof(R),
+                        (cuuint64_t)a.n * a.n * cw * sizeof(R), bstride};
+    cuuint32_t b5[5] = {(cuuint32_t)cw, a.axis == 1 ? (cuuint32_t)a.rows_box : 1u,
+                        a.axis == 1 ? 1u : (cuuint32_t)a.rows_box, 1u, 1u};
+    const CUresult r5 =
+        fn(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5,
+           const_cast<void *>(a.src), d5, s5, b5, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r5 == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+  }
   const CUresult r =
       fn(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
          const_cast<void *>(a.src), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -148,6 +148,27 @@ def test_strided_variants_bit_identical(gg):
     torch.cuda.empty_cache()
 
 
+def test_chunk_major_layout_bit_identical(gg):
+    """The chunk-major spectrum between the y passes (both tile widths of this
+    size: variant 0's eight columns and variant 2's four) gives the plain
+    layout's positions bit for bit."""
+    plan = gg.Plan(N, BOX, EH_NW, Z, "f32")
+    ref = [torch.empty((N, N, N), dtype=torch.float32, device="cuda") for _ in range(3)]
+    cur = [torch.empty((N, N, N), dtype=torch.float32, device="cuda") for _ in range(3)]
+    for a in (0, 2):
+        plan.set_variants([0, a, a, a, a, 0])
+        for lay, dst in ((False, ref), (True, cur)):
+            plan.set_layout(lay)
+            assert plan.layout() == lay
+            plan.zeldovich(seed=4, out={"psi": [None] * 3, "pos": dst, "vel": [None] * 3})
+            plan.sync()
+        for j in range(3):
+            assert torch.equal(cur[j], ref[j]), (a, j)
+    del ref, cur
+    plan.close()
+    torch.cuda.empty_cache()
+
+
 def test_merge_cut_planted_mode(gg):
     """Eq. 4 on the full-size grid (the x pass's cut instantiation, with the
     spectrum parked in shared memory and both outputs from one launch): with
