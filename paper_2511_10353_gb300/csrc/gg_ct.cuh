@@ -279,6 +279,7 @@ __device__ __forceinline__ void stage(int p, const TwT &tw, const Ld &ld,
   constexpr int NS = ns_of(K, SI, INV);
   constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
   asm volatile("" : "+r"(p));
+  __builtin_assume(p >= 0 && p < P);
   Cx<R> w1[NB];
   if constexpr (NS > 1 && powers_from_w1<R, RAD>()) {
 #pragma unroll
@@ -343,6 +344,7 @@ __device__ __forceinline__ void last_stage_regs(int p, const TwT &tw, const Ld &
   constexpr int P = N / E, NB = E / RAD, SPAN = N / RAD, TSTEP = N / (NS * RAD);
   static_assert(NS * RAD == N, "last stage");
   asm volatile("" : "+r"(p));
+  __builtin_assume(p >= 0 && p < P);
   Cx<R> w1[NB];
   if constexpr (NS > 1 && powers_from_w1<R, RAD>()) {
 #pragma unroll
@@ -401,6 +403,7 @@ __device__ __forceinline__ void last_two_stages_regs(int p, const TwT &tw,
   constexpr int SPANA = N / RA, TSA = N / (NSA * RA);
   static_assert(NSA == P * G && NSA * RA * RB == N, "register pair");
   asm volatile("" : "+r"(p));
+  __builtin_assume(p >= 0 && p < P);
   Cx<R> w1[NBA];
   if constexpr (sizeof(R) == 4) {
 #pragma unroll

@@ -136,6 +136,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     }
     int c = tid & (B - 1), p = tid / B;
     asm volatile("" : "+r"(c), "+r"(p));
+    __builtin_assume(c >= 0 && c < B && p >= 0 && p < P);
     int64_t rr, outer;
     int chunk;
     decode(t, rr, outer, chunk);
@@ -244,6 +245,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     }
     for (int o = 0; o < a.nout; ++o) {
       asm volatile("" : "+r"(c), "+r"(p));
+      __builtin_assume(c >= 0 && c < B && p >= 0 && p < P);
       C *d = reinterpret_cast<C *>(a.dst[o]) + gbase;
       auto st_glob = [&](int n, C v) { d[(int64_t)n * ostride] = v; };
       C W[E];
@@ -513,6 +515,7 @@ __device__ __forceinline__ void zfwd_body(const ZFwdArgs &a, int64_t t0, int64_t
   for (int64_t t = t0; t < tlimit; t += tstep) {
     int l = tid / P, p = tid - (tid / P) * P;
     asm volatile("" : "+r"(l), "+r"(p));
+    __builtin_assume(l >= 0 && l < L && p >= 0 && p < P);
     const int64_t line = t * L + l;
     // line counts stay below 2^32 (N <= 4096, the host bounds the batch)
     const uint32_t lpr = (uint32_t)(a.lines_per_real > 0 ? a.lines_per_real : a.nlines);
