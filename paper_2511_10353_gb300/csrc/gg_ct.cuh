@@ -542,6 +542,16 @@ template <typename R, int N, int V> struct AxisPolicy {
   // where it fits beside the tiles and the largest filter table
   static constexpr bool TW_SMEM = BIG && sizeof(R) == 4 && V != kPersistV &&
                                   SMEM_EST + N * CB + 4 * kInterpExact + 16 * kMaxInterpCells(N) <= 227 * 1024;
+  // The inverse outputs leave through a third (staging) tile and TMA stores
+  // instead of per-thread global stores, where that tile fits beside the two
+  // tiles, the twiddles and (filter: the x pass) the largest FP32 filter
+  // table for MINB CTAs per SM. Not with the spectrum parked in shared
+  // memory, nor in the persistent batched kernel.
+  __host__ __device__ static constexpr bool tma_st(bool filter) {
+    const int per_cta = SMEM_EST + N * B * CB + (TW_SMEM ? N * CB : 0) +
+                        (filter ? 4 * kInterpExact + 16 * kMaxInterpCells(N) : 0) + 1024;
+    return !SPILL && V != kPersistV && nstages(skey<R>(N)) > 1 && MINB * per_cta <= 228 * 1024;
+  }
 };
 
 // z passes: lines per tile, variant 0 ~256 threads (sized so that two dense

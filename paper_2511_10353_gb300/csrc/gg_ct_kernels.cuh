@@ -34,12 +34,21 @@ constexpr int kFiltArgs = 0, kFiltNone = 1, kFiltInterp = 2;
 // CTA's share of all tiles; the persistent batched kernel: one tile). It
 // returns false when a copy wait gave up (the error word then holds
 // GG_ETIMEOUT). `map` must live in parameter (grid-constant) memory.
+// TST: the inverse outputs go through the staging tile and TMA stores
+// (smap0 / smap1: the tensor maps of dst[0] / dst[1], in parameter memory).
+template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
+__host__ __device__ constexpr bool axis_tma_store() {
+  return MODE != kAxisFwd && ct::AxisPolicy<R, N, V>::tma_st(FILT != kFiltNone && sizeof(R) == 4);
+}
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
 __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs &a, int64_t t0,
-                                          int64_t tstep, int64_t tlimit) {
+                                          int64_t tstep, int64_t tlimit,
+                                          const CUtensorMap *smap0 = nullptr,
+                                          const CUtensorMap *smap1 = nullptr) {
   using C = Cx<R>;
   constexpr bool FWD = MODE != kAxisInv, INV = MODE != kAxisFwd;
   using Pol = ct::AxisPolicy<R, N, V>;
+  constexpr bool TST = axis_tma_store<R, N, V, MODE, CUT, FILT>();
   constexpr int K = ct::skey<R>(N);
   constexpr int B = Pol::B, E = Pol::E, P = Pol::P, HALF = N / 2, S = ct::nstages(K);
   constexpr int TILE = N * B;
@@ -53,8 +62,11 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
-  // interpolated filter (FP32): exact values, then Hermite cells, after the tiles
-  float *f_exact = reinterpret_cast<float *>(bufs + 2 * TILE_STRIDE);
+  // TST: the staging tile after the two tiles; then the interpolated filter
+  // (FP32): exact values, then Hermite cells
+  constexpr int NT = TST ? 3 : 2;
+  C *stg = bufs + 2 * TILE_STRIDE;
+  float *f_exact = reinterpret_cast<float *>(bufs + NT * TILE_STRIDE);
   float4 *f_cells = reinterpret_cast<float4 *>(f_exact + kInterpExact);
   const int tid = threadIdx.x;
   const int64_t per_real = (int64_t)N * INNER;
@@ -66,7 +78,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
   // large radices: the N twiddles in shared memory (15-31 loads a butterfly),
   // after the tiles and the filter table
   constexpr bool TW_SMEM = ct::AxisPolicy<R, N, V>::TW_SMEM;
-  C *tw_s = bufs + 2 * TILE_STRIDE + (interp ? (kInterpExact + 4 * kMaxInterpCells(N)) / 2 : 0);
+  C *tw_s = bufs + NT * TILE_STRIDE + (interp ? (kInterpExact + 4 * kMaxInterpCells(N)) / 2 : 0);
   if constexpr (TW_SMEM) {
     const C *src = reinterpret_cast<const C *>(a.tw);
     for (int i = tid; i < N; i += blockDim.x) tw_s[i] = src[i];
@@ -168,6 +180,9 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     if (!ok) {  // late: no other copy is in flight
       if (tid == 0 && tn < tlimit && !late && !a.test_skip_copy)
         mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr, a.wait_us);
+      if constexpr (TST) {
+        if (tid == 0) bulk_wait0();  // the staging tile's stores, before the CTA exits
+      }
       return false;
     }
     auto ld_smem = [&](int n) { return buf[n * B + c]; };
@@ -272,6 +287,10 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
         fence_proxy_async_smem();
         issue(tn, 0);
       }
+      // TST: the last stage writes the staging tile, which the previous
+      // output's stores must have finished reading (checked by their issuing
+      // thread before the barrier ahead of the remaining stages)
+      auto st_stg = [&](int n, C v) { stg[n * B + c] = v; };
       if constexpr (S == 1) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -279,20 +298,50 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
           for (int r = 0; r < RH; ++r) st_glob((p + P * b) * RH + r, W[b * RH + r]);
       } else if constexpr (FUSE) {
         ct::inverse_head_store<R, N, E>(p, W, st_work);
+        if constexpr (TST) {
+          if (tid == 0) bulk_wait_read0();
+        }
         __syncthreads();
         ct::stages<R, N, E, true, 2, S - 1>(p, tw, ld_work, st_work);
-        ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
+        if constexpr (TST) ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_stg);
+        else ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
       } else {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
           for (int r = 0; r < RH; ++r) wb[((p + P * b) * RH + r) * B + c] = W[b * RH + r];
+        if constexpr (TST) {
+          if (tid == 0) bulk_wait_read0();
+        }
         __syncthreads();
         ct::stages<R, N, E, true, 1, S - 1>(p, tw, ld_work, st_work);
-        ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
+        if constexpr (TST) ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_stg);
+        else ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
+      }
+      if constexpr (TST) {  // the tile to dst[o] by TMA, once every thread's values are in
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          const CUtensorMap *sm = o == 0 ? smap0 : smap1;
+#pragma unroll
+          for (int i = 0; i < N; i += Pol::ROWS_BOX) {
+            if (a.chunked_out) {
+              if (a.axis == 1) tma_store_5d(sm, stg + i * B, 0, i, (int)outer, chunk, (int)rr);
+              else tma_store_5d(sm, stg + i * B, 0, (int)outer, i, chunk, (int)rr);
+            } else if (a.axis == 1) {
+              tma_store_4d(sm, stg + i * B, chunk * B * 2, i, (int)outer, (int)rr);
+            } else {
+              tma_store_4d(sm, stg + i * B, chunk * B * 2, (int)outer, i, (int)rr);
+            }
+          }
+          bulk_commit();
+        }
       }
     }
     __syncthreads();
+  }
+  if constexpr (TST) {
+    if (tid == 0) bulk_wait0();  // the staging tile's stores, before the CTA exits
   }
   __syncthreads();
   if (tid == 0) {  // the caller may reuse the shared memory
@@ -304,8 +353,9 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
 
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
 __global__ void __launch_bounds__(ct::AxisPolicy<R, N, V>::THREADS, ct::AxisPolicy<R, N, V>::MINB)
-    k_axis_ct(const __grid_constant__ CUtensorMap map, const AxisArgs a) {
-  axis_body<R, N, V, MODE, CUT, FILT>(map, a, blockIdx.x, gridDim.x, INT64_MAX);
+    k_axis_ct(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap0,
+              const __grid_constant__ CUtensorMap smap1, const AxisArgs a) {
+  axis_body<R, N, V, MODE, CUT, FILT>(map, a, blockIdx.x, gridDim.x, INT64_MAX, &smap0, &smap1);
 }
 
 // ------------------------------------------------------------ z passes
@@ -594,17 +644,29 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   CUtensorMap map;
   cudaError_t e = make_map<R>(&map, a);
   if (e != cudaSuccess) return e;
+  // TMA stores: the maps of the outputs (same geometry, their own layout)
+  constexpr bool TST = axis_tma_store<R, N, V, MODE, CUT, FILT>();
+  CUtensorMap smap[2] = {map, map};
+  if constexpr (TST) {
+    if (a.nout > 2) return cudaErrorInvalidValue;
+    for (int o = 0; o < a.nout; ++o) {
+      AxisArgs b = a;
+      b.src = a.dst[o];
+      b.chunked_in = a.chunked_out;
+      if ((e = make_map<R>(&smap[o], b)) != cudaSuccess) return e;
+    }
+  }
   const size_t tile = ((size_t)N * Pol::B * 2 * sizeof(R) + 127) & ~(size_t)127;
   const bool interp = sizeof(R) == 4 && a.pre && a.interp;
   const size_t filt = interp ? (Pol::TW_SMEM ? kInterpExact * sizeof(float) + (size_t)kMaxInterpCells(N) * 16
                                               : kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16)
                              : 0;
-  const size_t smem = 128 + 2 * tile + filt + (Pol::TW_SMEM ? (size_t)N * 2 * sizeof(R) : 0);
+  const size_t smem = 128 + (TST ? 3 : 2) * tile + filt + (Pol::TW_SMEM ? (size_t)N * 2 * sizeof(R) : 0);
   if (interp && a.interp_cells > kMaxInterpCells(N)) return cudaErrorInvalidValue;
   auto kern = k_axis_ct<R, N, V, MODE, CUT, FILT>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t tiles = (int64_t)N * a.inner_chunks * (a.nbatch > 0 ? a.nbatch : 1);
-  kern<<<persistent_blocks(kern, Pol::THREADS, smem, tiles), Pol::THREADS, smem, s>>>(map, a);
+  kern<<<persistent_blocks(kern, Pol::THREADS, smem, tiles), Pol::THREADS, smem, s>>>(map, smap[0], smap[1], a);
   return cudaGetLastError();
 }
 
