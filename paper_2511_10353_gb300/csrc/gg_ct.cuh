@@ -261,10 +261,18 @@ __device__ __forceinline__ void stage_twiddles(Cx<R> *v, int k, Cx<R> w1, const 
 
 // Barrier of an in-place stage: none (the stage writes elsewhere), the whole
 // CTA, or the warp (when every transform lies within one warp).
-enum Sync : int { kSyncNone = 0, kSyncCta = 1, kSyncWarp = 2 };
-template <int SY> __device__ __forceinline__ void stage_barrier() {
-  if constexpr (SY == kSyncCta) __syncthreads();
-  else if constexpr (SY == kSyncWarp) __syncwarp();
+// kSyncCtaAsync: CTA barriers, the one after the stage's stores preceded by
+// a proxy fence (the stage's output is then read by a TMA store)
+enum Sync : int { kSyncNone = 0, kSyncCta = 1, kSyncWarp = 2, kSyncCtaAsync = 3 };
+template <int SY, bool AFTER_STORES = false> __device__ __forceinline__ void stage_barrier() {
+  if constexpr (SY == kSyncCtaAsync && AFTER_STORES) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+  } else if constexpr (SY == kSyncCta || SY == kSyncCtaAsync) {
+    __syncthreads();
+  } else if constexpr (SY == kSyncWarp) {
+    __syncwarp();
+  }
 }
 
 // One Stockham stage of a length-N transform, stage index SI of the forward
@@ -304,7 +312,7 @@ __device__ __forceinline__ void stage(int p, const TwT &tw, const Ld &ld,
 #pragma unroll
     for (int r = 0; r < RAD; ++r) st(base + r * NS, v[b * RAD + r]);
   }
-  stage_barrier<SY>();
+  stage_barrier<SY, true>();
 }
 
 // Stages FIRST .. LAST-1 in place in shared memory, barrier SY.

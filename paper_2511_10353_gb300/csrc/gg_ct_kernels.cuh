@@ -41,6 +41,12 @@ __host__ __device__ constexpr bool axis_tma_store() {
   return MODE != kAxisFwd && ct::AxisPolicy<R, N, V>::tma_st(FILT != kFiltNone && sizeof(R) == 4);
 }
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
+__host__ __device__ constexpr bool axis_tma_store_inplace() {
+  using Pol = ct::AxisPolicy<R, N, V>;
+  return MODE != kAxisFwd && Pol::SPILL && V != ct::kPersistV && ct::nstages(ct::skey<R>(N)) > 1 &&
+         !ct::fuse_pair<R, N, Pol::E>() && !axis_tma_store<R, N, V, MODE, CUT, FILT>();
+}
+template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
 __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs &a, int64_t t0,
                                           int64_t tstep, int64_t tlimit,
                                           const CUtensorMap *smap0 = nullptr,
@@ -59,6 +65,11 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
   constexpr int SPAN = N / RH, NB = E / RH;
   constexpr bool SPILL = Pol::SPILL;
   constexpr bool FUSE = ct::fuse_pair<R, N, E>();  // stage pairs around the hand-off in registers
+  // TSI: with the spectrum parked (no room for a staging tile), each inverse
+  // output's last stage runs in place in the work buffer and a TMA store
+  // copies it out; the buffer is rewritten once that store has read it
+  constexpr bool TSI = axis_tma_store_inplace<R, N, V, MODE, CUT, FILT>();
+  constexpr bool TMA_OUT = TST || TSI;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
@@ -142,7 +153,10 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     const int sb = late ? 0 : it & 1;
     const uint32_t phase = late ? (uint32_t)(it & 1) : (uint32_t)((it >> 1) & 1);
     const int64_t tn = t + tstep;
-    if (tid == 0 && tn < tlimit && !late) {
+    // the next tile's copy, into the other buffer; TSI with one output: later,
+    // once the previous tile's output store (from that buffer) has read it
+    const bool ahead = !late && !TSI;
+    if (tid == 0 && tn < tlimit && ahead) {
       fence_proxy_async_smem();
       issue(tn, sb ^ 1);
     }
@@ -178,10 +192,10 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     }
     const bool ok = __syncthreads_and(mbar_wait(&bars[sb], phase, a.err, a.wait_us));
     if (!ok) {  // late: no other copy is in flight
-      if (tid == 0 && tn < tlimit && !late && !a.test_skip_copy)
+      if (tid == 0 && tn < tlimit && ahead && !a.test_skip_copy)
         mbar_wait(&bars[sb ^ 1], (uint32_t)(((it + 1) >> 1) & 1), nullptr, a.wait_us);
-      if constexpr (TST) {
-        if (tid == 0) bulk_wait0();  // the staging tile's stores, before the CTA exits
+      if constexpr (TMA_OUT) {
+        if (tid == 0) bulk_wait0();  // the output stores, before the CTA exits
       }
       return false;
     }
@@ -281,8 +295,18 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
         for (int b = 0; b < NB; ++b) Butterfly<RH, true, C>::run(&W[b * RH]);  // inverse stage 0
       }
       // the previous output's last stage has read the work buffer; SPILL with
-      // one buffer: every thread has read its parked spectrum
-      if (o > 0 || (SPILL && !late)) __syncthreads();
+      // one buffer: every thread has read its parked spectrum; TSI: the
+      // previous output's store has read the work buffer
+      if constexpr (TSI) {
+        if (tid == 0) bulk_wait_read0();
+        __syncthreads();
+        if (!late && o == 0 && tid == 0 && tn < tlimit) {  // the other buffer is free now
+          fence_proxy_async_smem();
+          issue(tn, sb ^ 1);
+        }
+      } else {
+        if (o > 0 || (SPILL && !late)) __syncthreads();
+      }
       if (late && o == a.nout - 1 && tid == 0 && tn < tlimit) {  // the input buffer is free
         fence_proxy_async_smem();
         issue(tn, 0);
@@ -315,23 +339,31 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
         }
         __syncthreads();
         ct::stages<R, N, E, true, 1, S - 1>(p, tw, ld_work, st_work);
-        if constexpr (TST) ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_stg);
-        else ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
+        if constexpr (TST) {
+          ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_stg);
+        } else if constexpr (TSI) {  // in place: loads, barrier, stores, fence, barrier
+          ct::stage<R, N, E, S - 1, true, ct::kSyncCtaAsync>(p, tw, ld_work, st_work);
+        } else {
+          ct::stage<R, N, E, S - 1, true, ct::kSyncNone>(p, tw, ld_work, st_glob);
+        }
       }
-      if constexpr (TST) {  // the tile to dst[o] by TMA, once every thread's values are in
-        fence_proxy_async_smem();
-        __syncthreads();
+      if constexpr (TMA_OUT) {  // the tile to dst[o] by TMA, once every thread's values are in
+        const C *src_t = TST ? stg : wb;
+        if constexpr (TST) {
+          fence_proxy_async_smem();
+          __syncthreads();
+        }
         if (tid == 0) {
           const CUtensorMap *sm = o == 0 ? smap0 : smap1;
 #pragma unroll
           for (int i = 0; i < N; i += Pol::ROWS_BOX) {
             if (a.chunked_out) {
-              if (a.axis == 1) tma_store_5d(sm, stg + i * B, 0, i, (int)outer, chunk, (int)rr);
-              else tma_store_5d(sm, stg + i * B, 0, (int)outer, i, chunk, (int)rr);
+              if (a.axis == 1) tma_store_5d(sm, src_t + i * B, 0, i, (int)outer, chunk, (int)rr);
+              else tma_store_5d(sm, src_t + i * B, 0, (int)outer, i, chunk, (int)rr);
             } else if (a.axis == 1) {
-              tma_store_4d(sm, stg + i * B, chunk * B * 2, i, (int)outer, (int)rr);
+              tma_store_4d(sm, src_t + i * B, chunk * B * 2, i, (int)outer, (int)rr);
             } else {
-              tma_store_4d(sm, stg + i * B, chunk * B * 2, (int)outer, i, (int)rr);
+              tma_store_4d(sm, src_t + i * B, chunk * B * 2, (int)outer, i, (int)rr);
             }
           }
           bulk_commit();
@@ -340,8 +372,8 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     }
     __syncthreads();
   }
-  if constexpr (TST) {
-    if (tid == 0) bulk_wait0();  // the staging tile's stores, before the CTA exits
+  if constexpr (TMA_OUT) {
+    if (tid == 0) bulk_wait0();  // the output stores, before the CTA exits
   }
   __syncthreads();
   if (tid == 0) {  // the caller may reuse the shared memory
@@ -645,7 +677,8 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   cudaError_t e = make_map<R>(&map, a);
   if (e != cudaSuccess) return e;
   // TMA stores: the maps of the outputs (same geometry, their own layout)
-  constexpr bool TST = axis_tma_store<R, N, V, MODE, CUT, FILT>();
+  constexpr bool TST = axis_tma_store<R, N, V, MODE, CUT, FILT>() ||
+                       axis_tma_store_inplace<R, N, V, MODE, CUT, FILT>();
   CUtensorMap smap[2] = {map, map};
   if constexpr (TST) {
     if (a.nout > 2) return cudaErrorInvalidValue;
@@ -661,7 +694,8 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   const size_t filt = interp ? (Pol::TW_SMEM ? kInterpExact * sizeof(float) + (size_t)kMaxInterpCells(N) * 16
                                               : kInterpExact * sizeof(float) + (size_t)a.interp_cells * 16)
                              : 0;
-  const size_t smem = 128 + (TST ? 3 : 2) * tile + filt + (Pol::TW_SMEM ? (size_t)N * 2 * sizeof(R) : 0);
+  constexpr bool STAGING = axis_tma_store<R, N, V, MODE, CUT, FILT>();  // a third tile
+  const size_t smem = 128 + (STAGING ? 3 : 2) * tile + filt + (Pol::TW_SMEM ? (size_t)N * 2 * sizeof(R) : 0);
   if (interp && a.interp_cells > kMaxInterpCells(N)) return cudaErrorInvalidValue;
   auto kern = k_axis_ct<R, N, V, MODE, CUT, FILT>;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
