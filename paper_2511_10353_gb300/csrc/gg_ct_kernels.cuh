@@ -40,6 +40,13 @@ template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFilt
 __host__ __device__ constexpr bool axis_tma_store() {
   return MODE != kAxisFwd && ct::AxisPolicy<R, N, V>::tma_st(FILT != kFiltNone && sizeof(R) == 4);
 }
+// (only where the register budget is tight, Pol::SPILL: at 512 the plain
+// stores measured faster, 0.170 against 0.178 ms)
+template <typename R, int N, int V, int MODE>
+__host__ __device__ constexpr bool axis_tma_store_fwd() {
+  return MODE == kAxisFwd && V != ct::kPersistV && ct::nstages(ct::skey<R>(N)) > 1 &&
+         ct::AxisPolicy<R, N, V>::SPILL;
+}
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
 __host__ __device__ constexpr bool axis_tma_store_inplace() {
   using Pol = ct::AxisPolicy<R, N, V>;
@@ -69,7 +76,9 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
   // output's last stage runs in place in the work buffer and a TMA store
   // copies it out; the buffer is rewritten once that store has read it
   constexpr bool TSI = axis_tma_store_inplace<R, N, V, MODE, CUT, FILT>();
-  constexpr bool TMA_OUT = TST || TSI;
+  // TSF: forward only, the spectrum back into the tile buffer and out by TMA
+  constexpr bool TSF = axis_tma_store_fwd<R, N, V, MODE>();
+  constexpr bool TMA_OUT = TST || TSI || TSF;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   C *bufs = reinterpret_cast<C *>(smem_raw + 128);
@@ -155,7 +164,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     const int64_t tn = t + tstep;
     // the next tile's copy, into the other buffer; TSI with one output: later,
     // once the previous tile's output store (from that buffer) has read it
-    const bool ahead = !late && !TSI;
+    const bool ahead = !late && !TSI && !TSF;
     if (tid == 0 && tn < tlimit && ahead) {
       fence_proxy_async_smem();
       issue(tn, sb ^ 1);
@@ -205,6 +214,33 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
     auto st_work = [&](int n, C v) { wb[n * B + c] = v; };
     // SPILL, inverse only, no filter: the spectrum is already parked
     const bool x_regs = !SPILL || FWD || pre || !INV;
+    // the outputs by TMA: tile rows at the load's coordinates, from src_t
+    auto tma_out = [&](const C *src_t, int o) {
+      const CUtensorMap *sm = o == 0 ? smap0 : smap1;
+#pragma unroll
+      for (int i = 0; i < N; i += Pol::ROWS_BOX) {
+        if (a.chunked_out) {
+          if (a.axis == 1) tma_store_5d(sm, src_t + i * B, 0, i, (int)outer, chunk, (int)rr);
+          else tma_store_5d(sm, src_t + i * B, 0, (int)outer, i, chunk, (int)rr);
+        } else if (a.axis == 1) {
+          tma_store_4d(sm, src_t + i * B, chunk * B * 2, i, (int)outer, (int)rr);
+        } else {
+          tma_store_4d(sm, src_t + i * B, chunk * B * 2, (int)outer, i, (int)rr);
+        }
+      }
+      bulk_commit();
+    };
+    // TSF: the next tile's copy once the forward's first stages have run (the
+    // previous tile's store has read that buffer by then)
+    auto issue_after_stages = [&]() {
+      if constexpr (TSF) {
+        if (tid == 0 && tn < tlimit) {
+          bulk_wait_read0();
+          fence_proxy_async_smem();
+          issue(tn, sb ^ 1);
+        }
+      }
+    };
     C X[E];
     if constexpr (FWD) {
       if constexpr (FUSE) {
@@ -212,9 +248,11 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
           ct::stages_pingpong<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem, ld_work, st_work);
         else
           ct::stages<R, N, E, false, 0, S - 2>(p, tw, ld_smem, st_smem);
+        issue_after_stages();
         ct::last_two_stages_regs<R, N, E>(p, tw, ld_smem, X);
       } else {
         ct::stages<R, N, E, false, 0, S - 1>(p, tw, ld_smem, st_smem);
+        issue_after_stages();
         ct::last_stage_regs<R, N, E, false>(p, tw, ld_smem, X);
       }
     } else if (x_regs) {
@@ -253,12 +291,23 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
         }
     }
     if constexpr (!INV) {  // forward only: the spectrum to dst[0]
-      C *d = reinterpret_cast<C *>(a.dst[0]) + gbase;
+      if constexpr (TSF) {
+        __syncthreads();  // the last stage has read the tile: it becomes the output tile
 #pragma unroll
-      for (int b = 0; b < NB; ++b)
+        for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * ostride] = X[b * RH + r];
-      __syncthreads();
+          for (int r = 0; r < RH; ++r) buf[(p + P * b + r * SPAN) * B + c] = X[b * RH + r];
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) tma_out(buf, 0);
+      } else {
+        C *d = reinterpret_cast<C *>(a.dst[0]) + gbase;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int r = 0; r < RH; ++r) d[(int64_t)(p + P * b + r * SPAN) * ostride] = X[b * RH + r];
+        __syncthreads();
+      }
       continue;
     }
     if constexpr (SPILL) {
@@ -353,21 +402,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
           fence_proxy_async_smem();
           __syncthreads();
         }
-        if (tid == 0) {
-          const CUtensorMap *sm = o == 0 ? smap0 : smap1;
-#pragma unroll
-          for (int i = 0; i < N; i += Pol::ROWS_BOX) {
-            if (a.chunked_out) {
-              if (a.axis == 1) tma_store_5d(sm, src_t + i * B, 0, i, (int)outer, chunk, (int)rr);
-              else tma_store_5d(sm, src_t + i * B, 0, (int)outer, i, chunk, (int)rr);
-            } else if (a.axis == 1) {
-              tma_store_4d(sm, src_t + i * B, chunk * B * 2, i, (int)outer, (int)rr);
-            } else {
-              tma_store_4d(sm, src_t + i * B, chunk * B * 2, (int)outer, i, (int)rr);
-            }
-          }
-          bulk_commit();
-        }
+        if (tid == 0) tma_out(src_t, o);
       }
     }
     __syncthreads();
@@ -678,7 +713,8 @@ cudaError_t ct_launch_axis(const AxisArgs &in, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // TMA stores: the maps of the outputs (same geometry, their own layout)
   constexpr bool TST = axis_tma_store<R, N, V, MODE, CUT, FILT>() ||
-                       axis_tma_store_inplace<R, N, V, MODE, CUT, FILT>();
+                       axis_tma_store_inplace<R, N, V, MODE, CUT, FILT>() ||
+                       axis_tma_store_fwd<R, N, V, MODE>();
   CUtensorMap smap[2] = {map, map};
   if constexpr (TST) {
     if (a.nout > 2) return cudaErrorInvalidValue;
