@@ -678,15 +678,31 @@ __device__ __forceinline__ void zfwd_body(const ZFwdArgs &a, int64_t t0, int64_t
     } else {
       ct::stages<R, M, E, false, 0, S, Pol::SY>(p, tw_half, ld_w, st_w);
     }
+    // X_k = S/2 + D u_k with S = Z_k + conj Z_{M-k}, D = Z_k - conj Z_{M-k},
+    // u_k = -(i/2) w_k; the partner X_{M-k} = conj(S/2 - D u_k) (w_{M-k} =
+    // -conj w_k), so each thread takes the pairs k = p + P i < M/2 and both
+    // members from one pair of loads. k = 0: X_0 = Re Z_0 + Im Z_0 (real), and
+    // the self-paired X_{M/2} = conj Z_{M/2}.
+    static_assert(P * (E / 2) == M / 2, "r2c pairs");
     C *dst = reinterpret_cast<C *>(a.out) + line * M;
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
+    for (int i = 0; i < E / 2; ++i) {
       const int k = p + P * i;
       const C zk = work[zpad<LD, PAD>(l, k)];
-      const C zm = work[zpad<LD, PAD>(l, k ? M - k : 0)];
-      const C fe = {(R)0.5 * (zk.x + zm.x), (R)0.5 * (zk.y - zm.y)};
-      const C fo = {(R)0.5 * (zk.y + zm.y), (R)-0.5 * (zk.x - zm.x)};
-      dst[k] = cadd(fe, cmul(fo, ldg_c(twf + k)));
+      if (k == 0) {
+        const C zh = work[zpad<LD, PAD>(l, M / 2)];
+        dst[0] = C{zk.x + zk.y, (R)0};
+        dst[M / 2] = C{zh.x, -zh.y};
+      } else {
+        const C zm = work[zpad<LD, PAD>(l, M - k)];
+        const C w = ldg_c(twf + k);
+        const C u = {(R)0.5 * w.y, (R)-0.5 * w.x};  // exact: a halving and a swap
+        const C sm = {zk.x + zm.x, zk.y - zm.y};
+        const C df = {zk.x - zm.x, zk.y + zm.y};
+        const C t = cmul(df, u);
+        dst[k] = C{fma_rn((R)0.5, sm.x, t.x), fma_rn((R)0.5, sm.y, t.y)};
+        dst[M - k] = C{fma_rn((R)0.5, sm.x, -t.x), -fma_rn((R)0.5, sm.y, -t.y)};
+      }
     }
     ct::stage_barrier<Pol::SY>();  // the work tile's lines are rewritten next tile
   }

@@ -154,6 +154,8 @@ template <typename R> __device__ __forceinline__ R noise_cell(uint64_t seed, uin
 // Eq. 3 and the i m_z factor of the z inverse pass.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Periodic wrap of a coordinate into [0, L) (Eq. 3 positions).
 template <typename R>
