@@ -354,7 +354,8 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
           issue(tn, sb ^ 1);
         }
       } else {
-        if (o > 0 || (SPILL && !late)) __syncthreads();
+        // (TST: the previous output ended with a barrier after its last stage)
+        if (!TST && (o > 0 || (SPILL && !late))) __syncthreads();
       }
       if (late && o == a.nout - 1 && tid == 0 && tn < tlimit) {  // the input buffer is free
         fence_proxy_async_smem();
@@ -405,7 +406,9 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
         if (tid == 0) tma_out(src_t, o);
       }
     }
-    __syncthreads();
+    // (TST: the last output's barrier after its last stage already ordered
+    // every access to the tile buffers before the next copy into them)
+    if constexpr (!TST) __syncthreads();
   }
   if constexpr (TMA_OUT) {
     if (tid == 0) bulk_wait0();  // the output stores, before the CTA exits
