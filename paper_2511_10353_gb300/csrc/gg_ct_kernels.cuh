@@ -538,8 +538,8 @@ __device__ __forceinline__ bool zinv_body(const ZInvArgs &a, int64_t t0, int64_t
       fence_proxy_async_smem();
       issue(tn);
     }
-    ct::stages<R, M, E, true, HEAD, S - 1, Pol::SY>(p, tw_half, ld_w, st_w);
-    ct::last_stage_regs<R, M, E, true>(p, tw_half, ld_w, v);
+    ct::stages<R, M, E, true, HEAD, S - 1, Pol::SY | ct::kNoRangeHint>(p, tw_half, ld_w, st_w);
+    ct::last_stage_regs<R, M, E, true, false>(p, tw_half, ld_w, v);
     // line -> (realization, x, y): line counts stay below 2^32 (N <= 4096, the
     // host bounds the batch), so 32-bit divisions suffice
     const uint32_t line = (uint32_t)(t * L + l);
