@@ -278,13 +278,17 @@ gg_status upload_interp(gg_plan_t *plan, void **dst, const F &fm) {
     const double h = 1e-4 * std::max(1.0, x);
     return (fm(x + h, -1) - fm(x - h, -1)) / (2 * h);
   };
+  // per cell the cubic Hermite interpolant through f and f' at both ends,
+  // as its Taylor coefficients in t = m - j (FP64, rounded once), so that the
+  // kernels evaluate it by Horner's rule: a0 + t (a1 + t (a2 + t a3))
   for (int j = 0; j < cells; ++j) {
     const double x0 = std::max((double)j, 1.0), x1 = (double)j + 1.0;  // cells below 32 are unused
+    const double f0 = fm(x0, -1), d0 = d(x0), f1 = fm(x1, -1), d1 = d(x1);
     float *c = buf.data() + gg::kInterpExact + 4 * (size_t)j;
-    c[0] = (float)fm(x0, -1);
-    c[1] = (float)d(x0);
-    c[2] = (float)fm(x1, -1);
-    c[3] = (float)d(x1);
+    c[0] = (float)f0;
+    c[1] = (float)d0;
+    c[2] = (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1);
+    c[3] = (float)(2.0 * (f0 - f1) + d0 + d1);
   }
   plan->tab.interp_cells = cells;
   return upload(plan, dst, buf);

@@ -274,15 +274,13 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
             f = __ldg(table + q);
           } else if (q < kInterpExact) {
             f = (R)f_exact[q];
-          } else {  // cubic Hermite in m = sqrt(m2), unit cells
+          } else {  // cubic Hermite in m = sqrt(m2), unit cells, Horner form
             const float mf = (float)q;
             const float m = mf * rsqrtf(mf);
             const int j = (int)m;
             const float t = m - (float)j;
             const float4 cc = f_cells[j];
-            const float t2 = t * t, t3 = t2 * t;
-            f = (R)((2.f * t3 - 3.f * t2 + 1.f) * cc.x + (t3 - 2.f * t2 + t) * cc.y +
-                    (3.f * t2 - 2.f * t3) * cc.z + (t3 - t2) * cc.w);
+            f = (R)fmaf(t, fmaf(t, fmaf(t, cc.w, cc.z), cc.y), cc.x);
           }
           if constexpr (CUT) {
             if (q < a.qmin) f = (R)0;  // Eq. 4: large scales removed

@@ -72,7 +72,8 @@ struct AxisArgs {
   // FP32 size-specialised kernels: T from shared memory instead of a gather
   // from the global table: exact values for m2 < kInterpExact, above that a
   // cubic Hermite interpolation in m = sqrt(m2) over unit cells (float4:
-  // F_j, F'_j, F_j+1, F'_j+1). nullptr: gather from `table`.
+  // the interpolant's coefficients a0..a3 in t = m - j, from F_j, F'_j,
+  // F_j+1, F'_j+1). nullptr: gather from `table`.
   const void *interp;
   int interp_cells;
   int e;                  // elements per thread (multiple of every radix)
