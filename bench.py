@@ -11,7 +11,7 @@ s8=.8), z = 100, FP32, outputs pos + vel (3 + 3 grids). The working set
 (>= 4.3 GB) is far larger than the 129 MB L2, so no flush is needed. The
 default run also times the 1536^3 precision workload (2000 Mpc/h,
 Eisenstein-Hu no-wiggle, z = 100) with its FP64 path and FP32 error under
-the key "north_star_1536" (--no-north-star skips it), and the oracle on the
+the key "zeldovich_1536_fp32" (--no-1536 skips it), and the oracle on the
 whole 512^3 workload as the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-north-star", action="store_true",
+    ap.add_argument("--no-1536", action="store_true",
                     help="skip the 1536^3 leg of the default run")
     ap.add_argument("--variants", default=None,
                     help="comma list of 6 tile variants instead of autotuning (profiling runs)")
@@ -738,7 +738,7 @@ def main():
 
     # the 1536^3 precision workload (EH no-wiggle, 2000 Mpc/h), timed in the
     # same run when the headline workload is the default 512^3 one
-    if args.workload == "zeldovich_512_fp32" and not args.no_north_star:
+    if args.workload == "zeldovich_512_fp32" and not args.no_1536:
         w2 = dict(WORKLOADS["zeldovich_1536_fp32"])
         k2 = max(10, min(20, args.steps))
         res2, plan2, _ = time_plain(gg, w2, k2, min(args.warmup, 3), None, world, barrier,
@@ -751,7 +751,7 @@ def main():
             plan2.close()
         del plan2
         torch.cuda.empty_cache()
-        line["north_star_1536"] = ns
+        line["zeldovich_1536_fp32"] = ns
         line["gpu_launches"] += res2["gpu_launches"]
 
     if world == 1 and not args.no_cpu_baseline:
