@@ -271,7 +271,9 @@ void filter_values(const gg_params *p, const gg::cosmo::Model &m, double growth,
 template <class F>
 gg_status upload_interp(gg_plan_t *plan, void **dst, const F &fm) {
   const int64_t n = plan->p.n;
-  const int cells = (int)std::ceil(std::sqrt(3.0) * (double)(n / 2)) + 2;
+  // cells j = kInterpFirstCell ... (m2 >= kInterpExact reads no lower cell)
+  const int last = (int)std::ceil(std::sqrt(3.0) * (double)(n / 2)) + 2;
+  const int cells = std::max(0, last - gg::kInterpFirstCell);
   std::vector<float> buf(gg::kInterpExact + 4 * (size_t)cells);
   for (int q = 0; q < gg::kInterpExact; ++q) buf[q] = (float)fm(std::sqrt((double)q), q);
   auto d = [&](double x) {
@@ -281,10 +283,11 @@ gg_status upload_interp(gg_plan_t *plan, void **dst, const F &fm) {
   // per cell the cubic Hermite interpolant through f and f' at both ends,
   // as its Taylor coefficients in t = m - j (FP64, rounded once), so that the
   // kernels evaluate it by Horner's rule: a0 + t (a1 + t (a2 + t a3))
-  for (int j = 0; j < cells; ++j) {
-    const double x0 = std::max((double)j, 1.0), x1 = (double)j + 1.0;  // cells below 32 are unused
+  for (int i = 0; i < cells; ++i) {
+    const int j = gg::kInterpFirstCell + i;
+    const double x0 = (double)j, x1 = (double)j + 1.0;
     const double f0 = fm(x0, -1), d0 = d(x0), f1 = fm(x1, -1), d1 = d(x1);
-    float *c = buf.data() + gg::kInterpExact + 4 * (size_t)j;
+    float *c = buf.data() + gg::kInterpExact + 4 * (size_t)i;
     c[0] = (float)f0;
     c[1] = (float)d0;
     c[2] = (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1);

@@ -534,8 +534,18 @@ template <typename R, int N, int V> struct AxisPolicy {
   // pass may still keep that pass at one); variant 1 of the large radices:
   // as many CTAs as the tiles' shared memory allows, up to three
   static constexpr int SMEM_EST = 128 + 2 * N * B * CB;
+  // variant 2 of the FP32 large radices from N = 512, where the two tiles
+  // and the largest filter table of three CTAs fit an SM: three CTAs with
+  // the spectrum in registers (the outputs leave by TMA from the tile buffer
+  // itself, the twiddles stay in global memory). 512^3 x pass 0.454 ->
+  // 0.421 ms; at N = 256 the two-CTA staging-tile form stays (the batched
+  // workload measured 17.0 against 17.4 ms with three CTAs there too)
+  static constexpr bool THREE = V == 2 && BIG && sizeof(R) == 4 && N >= 512 &&
+                                3 * (SMEM_EST + 4 * kInterpExact + 16 * kMaxInterpCells(N) + 1024) <=
+                                    228 * 1024;
   static constexpr int min_blocks() {
     if (V == kPersistV) return 2;
+    if (THREE) return 3;
     if (BIG && V == 1) {  // the x pass's filter table (about 11 KB) may still cost one
       const int by_smem = (228 * 1024) / (SMEM_EST + 1024);
       return by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
@@ -546,12 +556,12 @@ template <typename R, int N, int V> struct AxisPolicy {
   static constexpr int REG_BUDGET =
       65536 / (THREADS * MINB) < 255 ? 65536 / (THREADS * MINB) : 255;
   static constexpr int REG_NEED = 4 * E * ((int)sizeof(R) / 4) + 48;
-  static constexpr bool SPILL = (BIG && V == 1) || REG_NEED > REG_BUDGET;
+  static constexpr bool SPILL = (BIG && V == 1) || (!THREE && REG_NEED > REG_BUDGET);
   static constexpr int ROWS_BOX = N <= 256 ? N : (N % 256 == 0 ? 256 : (N % 192 == 0 ? 192 : 128));
   static_assert(V != kPersistV || (THREADS == 256 && (N / 2) % B == 0), "persistent tile");
   // the large radices read their stage twiddles from a shared-memory copy
   // where it fits beside the tiles and the largest filter table
-  static constexpr bool TW_SMEM = BIG && sizeof(R) == 4 && V != kPersistV &&
+  static constexpr bool TW_SMEM = BIG && sizeof(R) == 4 && V != kPersistV && !THREE &&
                                   SMEM_EST + N * CB + 4 * kInterpExact + 16 * kMaxInterpCells(N) <= 227 * 1024;
   // The inverse outputs leave through a third (staging) tile and TMA stores
   // instead of per-thread global stores, where that tile fits beside the two
@@ -561,7 +571,7 @@ template <typename R, int N, int V> struct AxisPolicy {
   __host__ __device__ static constexpr bool tma_st(bool filter) {
     const int per_cta = SMEM_EST + N * B * CB + (TW_SMEM ? N * CB : 0) +
                         (filter ? 4 * kInterpExact + 16 * kMaxInterpCells(N) : 0) + 1024;
-    return !SPILL && V != kPersistV && nstages(skey<R>(N)) > 1 && MINB * per_cta <= 228 * 1024;
+    return !SPILL && !THREE && V != kPersistV && nstages(skey<R>(N)) > 1 && MINB * per_cta <= 228 * 1024;
   }
 };
 

@@ -50,7 +50,8 @@ __host__ __device__ constexpr bool axis_tma_store_fwd() {
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
 __host__ __device__ constexpr bool axis_tma_store_inplace() {
   using Pol = ct::AxisPolicy<R, N, V>;
-  return MODE != kAxisFwd && Pol::SPILL && V != ct::kPersistV && ct::nstages(ct::skey<R>(N)) > 1 &&
+  return MODE != kAxisFwd && (Pol::SPILL || Pol::THREE) && V != ct::kPersistV &&
+         ct::nstages(ct::skey<R>(N)) > 1 &&
          !ct::fuse_pair<R, N, Pol::E>() && !axis_tma_store<R, N, V, MODE, CUT, FILT>();
 }
 template <typename R, int N, int V, int MODE, bool CUT = false, int FILT = kFiltArgs>
@@ -279,7 +280,7 @@ __device__ __forceinline__ bool axis_body(const CUtensorMap &map, const AxisArgs
             const float m = mf * rsqrtf(mf);
             const int j = (int)m;
             const float t = m - (float)j;
-            const float4 cc = f_cells[j];
+            const float4 cc = f_cells[j - kInterpFirstCell];
             f = (R)fmaf(t, fmaf(t, fmaf(t, cc.w, cc.z), cc.y), cc.x);
           }
           if constexpr (CUT) {

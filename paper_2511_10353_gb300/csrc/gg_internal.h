@@ -13,8 +13,15 @@ namespace gg {
 
 constexpr int kMaxStages = 16;
 constexpr int kInterpExact = 1024;  // m2 below this: exact table values in shared memory
-// most unit cells in m = sqrt(m2) of the interpolated filter for grids of n points
-__host__ __device__ constexpr int kMaxInterpCells(int n) { return (int)(1.7320508075688772 * (n / 2)) + 3; }
+// first stored unit cell in m = sqrt(m2) of the interpolated filter: m2 >= 1024
+// gives m >= 32 (31 for an FP32 square root just below 32)
+constexpr int kInterpFirstCell = 31;
+// most stored cells (j = kInterpFirstCell ...) for grids of n points
+__host__ __device__ constexpr int kMaxInterpCells(int n) {
+  return (int)(1.7320508075688772 * (n / 2)) + 3 - kInterpFirstCell > 0
+             ? (int)(1.7320508075688772 * (n / 2)) + 3 - kInterpFirstCell
+             : 0;
+}
 
 // Radix schedule of one complex transform of length `len` done inside a CTA
 // (Stockham autosort, decimation in time). Stage s combines radix[s] partial
